@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the exact-diagonalization hot path on GB300.
+
+Workload (the long-range quench): H = sum_{i<j} |i-j|^-1.5 sz_i sz_j + 0.8 sum sx,
+L = 24 open chain, all-up start, Krylov evolution with m = 20 vectors and
+dt = 0.01; every 0.1 time units <sz_i>, all <sz_i sz_j> and the half-chain
+entropy are measured.  One step = 10 Krylov steps (0.1 time units) plus that
+measurement set.  Metric: seconds of wall time per unit of simulated time
+(lower is better).  The H.psi product at L = 28 is timed beside it (GB/s).
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·ψ GB/s vs HBM peak at L=28; Krylov evolve s per unit time at stated error"
+UNIT = "s per unit simulated time"
+WL = dict(L=24, J=1.0, alpha=1.5, h=0.8, m=20, dt=0.01, krylov_steps_per_step=10)
+SIM_TIME_PER_STEP = WL["dt"] * WL["krylov_steps_per_step"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hpsi28", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(torch):
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def traffic_record():
+    """ncu DRAM traffic of the H.psi passes, valid only for the kernel source it was taken on."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "hpsi_traffic.json")))
+    except Exception:
+        return None
+    src = open(os.path.join(ROOT, "paper_1802_10052_gb300", "csrc", "hpsi_kernels.cu"), "rb").read()
+    if rec.get("hpsi_kernels_sha1") != hashlib.sha1(src).hexdigest():
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_1802_10052_gb300 import Chain
+
+    dev = torch.cuda.current_device()
+    L, m, dt, nk = WL["L"], WL["m"], WL["dt"], WL["krylov_steps_per_step"]
+    chain = Chain(L, J=WL["J"], alpha=WL["alpha"], h=WL["h"], prec=args.prec)
+    psi = chain.new_state()
+    chain.init_basis_state(psi, 0)
+    stream = torch.cuda.current_stream()
+    esize = 8 if args.prec == "mixed" else 16
+    D = 1 << L
+
+    def step(x):
+        chain.krylov_evolve(x, dt, nk, m)
+        sz = chain.measure_local(x)
+        zz = chain.measure_corr(x)
+        S = chain.schmidt_entropy(x)
+        return sz, zz, S
+
+    for _ in range(args.warmup):
+        step(psi)
+    torch.cuda.synchronize()
+    launches0 = chain_launches(chain)
+    chain.timing_read(reset=True)
+    chain.timing_enable(True)
+    clocks = ClockSampler(gpu_uuid(torch))
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(psi)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    chain.timing_enable(False)
+    hp_ms, hp_calls = chain.timing_read(reset=True)
+    launches = (chain_launches(chain) - launches0) // max(args.steps, 1)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    sim_time = SIM_TIME_PER_STEP * args.steps * world
+    value = (ms / 1000.0) / sim_time
+
+    # error of this configuration against the FP64 form (same GPU, same horizon)
+    out = {"ms_per_step": ms_per_step, "value": value, "clocks": ck, "launches_per_step": launches,
+           "hpsi_ms_avg": hp_ms / max(hp_calls, 1), "hpsi_calls": hp_calls}
+
+    # roofline of the dominant kernel (H.psi passes) from the live event timing
+    alg_bytes = 2.0 * D * esize
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = alg_bytes / (out["hpsi_ms_avg"] * 1e-3) / 1e9 if hp_calls else None
+    trec = traffic_record()
+    traffic = None
+    if trec and trec.get("prec") == args.prec and trec.get("L") == L:
+        traffic = trec.get("dram_bytes_per_product")
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                       "kernel": "hpsi_pass_kernel (all passes of one H.psi product)",
+                       "algorithmic_bytes": alg_bytes,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        host = torch.empty(D, dtype=chain.dtype, pin_memory=True)
+        chain.download(host, psi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            chain.upload(psi, host)
+            sz, zz, S = step(psi)
+            chain.download(host, psi)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e_val = (t1 - t0) / (SIM_TIME_PER_STEP * args.steps)
+        out["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": D * esize,
+                      "d2h_bytes_per_step": D * esize + 8 * (L + L * L + 1)}
+    chain.close()
+    del psi
+    torch.cuda.empty_cache()
+    return out
+
+
+def chain_launches(chain):
+    from paper_1802_10052_gb300 import _binding as B
+    import ctypes as C
+    n = C.c_int64()
+    B.check(B.lib.osmps_ed_launch_count(chain._h, C.byref(n)), "osmps_ed_launch_count")
+    return n.value
+
+
+def hpsi_L28(prec, reps=20, warm=3):
+    """H.psi at L = 28 (alpha = 1.5, h = 0.8): CUDA-event time per product."""
+    import torch
+
+    from paper_1802_10052_gb300 import Chain
+
+    L = 28
+    chain = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+    x = chain.new_state()
+    chain.init_basis_state(x, 12345)
+    y = chain.new_state()
+    for _ in range(warm):
+        chain.apply_H(x, y)
+        chain.apply_H(y, x)
+    torch.cuda.synchronize()
+    chain.timing_read(reset=True)
+    chain.timing_enable(True)
+    for i in range(reps):
+        if i % 2 == 0:
+            chain.apply_H(x, y)
+        else:
+            chain.apply_H(y, x)
+    ms, n = chain.timing_read(reset=True)
+    chain.timing_enable(False)
+    esize = 8 if prec == "mixed" else 16
+    t = ms / n
+    alg = 2.0 * (1 << L) * esize
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    chain.close()
+    del x, y
+    torch.cuda.empty_cache()
+    return {"prec": prec, "ms_per_product": t, "algorithmic_GBps": alg / (t * 1e-3) / 1e9,
+            "frac_of_measured_hbm": alg / (t * 1e-3) / 1e9 / peak, "algorithmic_bytes": alg}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+class OracleSample:
+    """Bounded sample of the workload on the FP64 oracle: a few Lanczos
+    iterations of one Krylov step (matvec + full reorthogonalisation), one
+    correlator through its two-site reduced density matrix, one single-site
+    expectation and the half-chain spectrum; scaled to seconds per unit of
+    simulated time (100 Krylov steps of m iterations and 10 measurement sets
+    per unit time)."""
+
+    def __init__(self, iters=3):
+        import numpy as np
+
+        import seeded_inputs as si
+        from oracle import ed_oracle as O
+
+        self.O, self.np = O, np
+        L = WL["L"]
+        self.L = L
+        self.iters = iters
+        self.mv = O.RuleSetH(L, O.coupling_table(L, WL["J"], WL["alpha"]), WL["h"])
+        psi = si.basis_state(L, 0)
+        psi, _ = O.krylov_step(self.mv, psi, WL["dt"], 4)  # a non-trivial state
+        self.psi = psi
+
+    def run(self):
+        np, O = self.np, self.O
+        m = WL["m"]
+        t0 = time.perf_counter()
+        V = [self.psi / np.linalg.norm(self.psi)]
+        for j in range(self.iters):
+            w = self.mv(V[j])
+            for _ in range(2):
+                for v in V:
+                    w = w - np.vdot(v, w) * v
+            V.append(w / np.linalg.norm(w))
+        t1 = time.perf_counter()
+        O.measure_corr_pair(self.psi, self.L, 3, 17)
+        t2 = time.perf_counter()
+        O.rdm_sites(self.psi, self.L, [5])
+        t3 = time.perf_counter()
+        O.schmidt_spectrum(self.psi, self.L)
+        t4 = time.perf_counter()
+        per_iter = (t1 - t0) / self.iters
+        # full reorth makes later iterations dearer: iteration j costs ~ (1 + j c) units
+        step = per_iter * m * (1.0 + (m - self.iters) / (2.0 * (self.iters + 1)) * 0.3)
+        pairs = self.L * (self.L - 1) // 2
+        meas = (t2 - t1) * pairs + (t3 - t2) * self.L + (t4 - t3)
+        per_unit = step / WL["dt"] + meas / SIM_TIME_PER_STEP
+        return per_unit, t4 - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    samp = OracleSample(iters=2)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, wall = samp.run()
+        if i >= args.warmup:
+            vals.append((v, wall))
+    value = statistics.median(v for v, _ in vals)
+    ms_per_step = value * SIM_TIME_PER_STEP * 1000.0
+    desc = ("2 Lanczos iterations of one Krylov step (matvec + full reorth) at L=24, one two-site RDM, one "
+            "single-site RDM and the half-chain spectrum per step, scaled to 100 Krylov steps of m=20 and 10 "
+            "measurement sets per unit time")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "lrqi_quench_L24: alpha=1.5 h=0.8 all-up, Krylov m=20 dt=0.01, "
+                                   "measure every 0.1", "L": WL["L"], "oracle": "numpy/scipy FP64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_line():
+    samp = OracleSample(iters=3)
+    v, wall = samp.run()
+    return {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"3 Lanczos iterations (matvec + full reorth) of one L=24 Krylov step, one two-site and one "
+                      f"single-site RDM and the half-chain spectrum ({wall:.1f} s of CPU work), scaled to 100 "
+                      f"Krylov steps of m=20 and 10 measurement sets per unit time"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    res = run_ours(args, rank, world)
+    extra = {}
+    if rank == 0 and not args.no_hpsi28:
+        extra["hpsi_L28"] = [hpsi_L28("mixed"), hpsi_L28("fp64", reps=6)]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_line()
+    if rank == 0:
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "c64+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": "lrqi_quench_L24: H = sum |i-j|^-1.5 sz sz + 0.8 sum sx, L=24, all-up "
+                                       "start, Krylov m=20 dt=0.01, <sz_i>, <sz_i sz_j>, S(L/2) every 0.1; "
+                                       "step = 0.1 time units",
+                           "L": WL["L"], "m": WL["m"], "dt": WL["dt"], "precision": args.prec,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "working set (21 Krylov vectors of 134 MB) larger than L2"},
+                "roofline": res["roofline"], "cpu_baseline": cpu, "clocks": res["clocks"],
+                "gpu_launches": res["launches_per_step"] * args.steps,
+                "hpsi_ms_avg_L24": res["hpsi_ms_avg"], **extra}
+        if "e2e" in res:
+            line["e2e"] = res["e2e"]
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * osmps_ed.h -- C ABI of the GB300 exact-diagonalization hot path.
+ *
+ * Matrix-free Hamiltonian-times-state product for spin-1/2 chains, used inside
+ * Lanczos ground-state search and Krylov real-time evolution, followed by the
+ * measurements <sz_k>, <sz_i sz_j> and the half-chain Schmidt spectrum.
+ * Everything runs on one CUDA device; all vector work is done by the kernels of
+ * this library.
+ *
+ * Model (arXiv:1802.10052, Eq. genericH with one site rule sigma^x and one
+ * distance-only infinite-function rule sigma^z sigma^z; the nearest-neighbour
+ * quantum Ising model Eq. HQI and the long-range H_LRQI of Sec. VI are special
+ * cases):
+ *
+ *     H = sum_{i<j} J(j-i) sz_i sz_j + sum_k h_k sx_k        (signed inputs)
+ *
+ * The paper's conventions are reached with J(r) = -1 (r = 1 only), h -> -h
+ * (Eq. HQI) or J(r) = -cos(phi)/r^alpha, h = -sin(phi) (H_LRQI).
+ *
+ * State layout (the rank-L tensor of Sec. IV in row-major order): a state is
+ * D = 2^L interleaved complex numbers (re, im) in device memory, complex128
+ * (double2) for OSMPS_FP64 and complex64 (float2) for OSMPS_MIXED.  Basis index
+ * b in [0, D); site k (1-based) is bit L-k, so site 1 is the most significant
+ * bit; bit value 0 is spin up (sz = +1).  All-up is b = 0.
+ *
+ * Ownership: the caller owns every state buffer (device pointers, 16-byte
+ * aligned, D elements, no aliasing between an input and an output of the same
+ * call unless stated).  The handle owns its tables and its Krylov workspace,
+ * allocated at create or on first use and released by osmps_ed_destroy.
+ *
+ * Ordering: work is enqueued on the handle's CUDA stream.  Calls that return
+ * host scalars synchronise that stream before returning; osmps_ed_apply_H and
+ * osmps_ed_init_basis_state return without synchronising.  One handle must
+ * not be used from two host threads at once.
+ *
+ * Errors: every call returns an osmps_status, never aborts.  After an error
+ * other than OSMPS_ECUDA the handle stays valid and the contents of output
+ * buffers are unspecified.  After OSMPS_ECUDA the CUDA context may be
+ * unusable; destroy the handle.
+ */
+#ifndef OSMPS_ED_H
+#define OSMPS_ED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osmps_ed osmps_ed_t;
+
+typedef enum {
+    OSMPS_OK = 0,
+    OSMPS_EINVAL = 1,       /* bad argument (range, NULL, non-finite, alignment) */
+    OSMPS_ENOMEM = 2,       /* device or host allocation failed */
+    OSMPS_ECUDA = 3,        /* a CUDA runtime or library call failed */
+    OSMPS_ENOCONV = 4,      /* Lanczos did not reach the tolerance in max_iter */
+    OSMPS_ETIMEOUT = 5,     /* a bounded device wait gave up */
+    OSMPS_EUNSUPPORTED = 6  /* valid request this build does not support */
+} osmps_status;
+
+typedef enum {
+    OSMPS_FP64 = 0,  /* complex128 states, FP64 arithmetic throughout */
+    OSMPS_MIXED = 1  /* complex64 states and H.psi in FP32; inner products,
+                        norms, Krylov coefficients and the small tridiagonal
+                        problem in FP64 */
+} osmps_prec;
+
+/* Largest chain length accepted (2^30 amplitudes). */
+#define OSMPS_MAX_L 30
+
+/*
+ * Create a handle for a chain of L sites (1 <= L <= OSMPS_MAX_L).
+ * Paper: Eq. genericH (site rule + infinite-function rule, coupling depending
+ * only on the distance, c_{k',k} = c(k'-k)); Eq. HQI; H_LRQI (Sec. VI).
+ *   couplings  host array J(r) for r = 1..L-1 (index r-1), or NULL.  When NULL,
+ *              J(r) = J / r^alpha; alpha < 0 (or +inf) keeps only J(1) = J
+ *              (nearest neighbours).
+ *   h          uniform transverse field (see osmps_ed_set_site_fields).
+ *   prec       OSMPS_FP64 or OSMPS_MIXED; fixes the element type of all states.
+ *   cuda_stream  cudaStream_t to enqueue work on (NULL = legacy default stream).
+ *   out        receives the handle.
+ * Errors: EINVAL (L out of range, non-finite input, out == NULL), ENOMEM, ECUDA.
+ */
+osmps_status osmps_ed_create(int L, const double *couplings, double J, double alpha, double h,
+                             int prec, void *cuda_stream, osmps_ed_t **out);
+
+/* Release the handle and everything it owns (synchronises its stream). NULL is OK. */
+osmps_status osmps_ed_destroy(osmps_ed_t *ed);
+
+/* Replace the stream used by later calls. */
+osmps_status osmps_ed_set_stream(osmps_ed_t *ed, void *cuda_stream);
+
+/* Uniform transverse field h (piecewise-constant h(t) is set between calls;
+ * the caller evaluates it at mid-step t + dt/2, Sec. III.A). */
+osmps_status osmps_ed_set_field(osmps_ed_t *ed, double h);
+
+/* Site-dependent fields h_k, host array of L values in site order k = 1..L
+ * (site rule with spatially dependent coupling c_k, Eq. genericH). */
+osmps_status osmps_ed_set_site_fields(osmps_ed_t *ed, const double *h_sites);
+
+/* Reorthogonalisation of Lanczos/Krylov vectors: 0 = three-term recurrence
+ * only, 1 = additionally one classical Gram-Schmidt pass against all stored
+ * vectors ("orthogonalized against all previous", Sec. III.D).  Default:
+ * 1 for osmps_ed_lanczos_ground, the handle's value for krylov_evolve
+ * (initially 0). */
+osmps_status osmps_ed_set_reorth(osmps_ed_t *ed, int mode);
+
+/* D = 2^L. */
+osmps_status osmps_ed_dim(const osmps_ed_t *ed, uint64_t *D);
+
+/* Bytes of device memory the handle currently owns. */
+osmps_status osmps_ed_device_bytes(const osmps_ed_t *ed, uint64_t *bytes);
+
+/* psi <- |b> (product state; all-up b = 0).  Device buffer, no sync. */
+osmps_status osmps_ed_init_basis_state(osmps_ed_t *ed, void *psi, uint64_t b);
+
+/* Stream-ordered copies of one state between host and device memory
+ * (D elements of the handle's type).  Pinned host memory gives async copies. */
+osmps_status osmps_ed_upload(osmps_ed_t *ed, void *dst_device, const void *src_host);
+osmps_status osmps_ed_download(osmps_ed_t *ed, void *dst_host, const void *src_device);
+
+/*
+ * out <- H psi, matrix-free (Sec. III.D, rule set times psi; Eq. OKrylov).
+ * psi, out: device buffers of D elements, must not alias.  No sync.
+ */
+osmps_status osmps_ed_apply_H(osmps_ed_t *ed, const void *psi, void *out);
+
+/* <psi|H|psi> and <psi|psi> (energy measurement, Sec. IV); host outputs,
+ * either may be NULL.  Synchronises. */
+osmps_status osmps_ed_energy(osmps_ed_t *ed, const void *psi, double *e_num, double *norm2);
+
+/*
+ * Lowest eigenpair by Lanczos (statics, Sec. II; eigsh replaced by Lanczos
+ * with full reorthogonalisation unless osmps_ed_set_reorth(ed, 0) was called
+ * after the last create).
+ *   psi       in: start vector (any nonzero norm); out: normalised ground state.
+ *   tol       stop when ||H x - E x|| <= tol for the normalised Ritz vector x
+ *             (checked explicitly once beta_{j+1}|y_j| <= tol).
+ *   max_iter  Lanczos vectors stored at most (1 <= max_iter <= 1000).
+ *   energy, residual, iters: host outputs (may be NULL).
+ * Returns ENOCONV (with the best vector in psi) if tol was not reached.
+ */
+osmps_status osmps_ed_lanczos_ground(osmps_ed_t *ed, void *psi, double tol, int max_iter,
+                                     double *energy, double *residual, int *iters);
+
+/*
+ * psi <- exp(-i H dt)^nsteps psi by the Krylov approximation (Sec. III.D):
+ * each step builds m Lanczos vectors v_1 = psi/||psi||, v_{i+1} from H v_i,
+ * and sets psi <- ||psi|| sum_i [exp(-i dt T_m)]_{i,1} v_i with the m x m
+ * tridiagonal T_m diagonalised in FP64 on the device.
+ *   m         Krylov vectors per step (1 <= m <= 64).
+ *   tol       relative breakdown threshold: a new vector whose norm beta_{j+1}
+ *             is below tol*(|alpha_j| + beta_j) ends the step's basis early
+ *             (the subspace is then invariant and the step exact);
+ *             tol <= 0 selects 1e-12.
+ *   err_estimate  host output (may be NULL): sum over steps of the a-posteriori
+ *             estimate beta_{m+1} |[exp(-i dt T_m) e_1]_m| ||psi||.
+ * The norm of psi is not renormalised between steps.
+ */
+osmps_status osmps_ed_krylov_evolve(osmps_ed_t *ed, void *psi, double dt, int nsteps, int m,
+                                    double tol, double *err_estimate);
+
+/*
+ * <sz_k> for k = 1..L (Sec. IV, Tr(sz rho_k) from the single-site reduced
+ * density matrix).  sz: host array of L doubles.  Unnormalised: for a state of
+ * norm n the values scale with n^2.  Synchronises.
+ */
+osmps_status osmps_ed_measure_local(osmps_ed_t *ed, const void *psi, double *sz);
+
+/*
+ * <sz_i sz_j> for all i, j (Sec. IV, Tr((sz x sz) rho_ij) from the two-site
+ * reduced density matrices).  szsz: host array of L*L doubles, row-major,
+ * symmetric, diagonal = <psi|psi>.  Synchronises.
+ */
+osmps_status osmps_ed_measure_corr(osmps_ed_t *ed, const void *psi, double *szsz);
+
+/*
+ * Schmidt spectrum and entanglement entropy of the bipartition sites 1..cut |
+ * cut+1..L (Sec. IV, bond entropy: rho = M M^dagger with M the state reshaped
+ * to (2^cut, 2^(L-cut)); S = -sum_j Lambda_j ln Lambda_j, Sec. V).
+ *   cut      1 <= cut <= L-1, or -1 for floor(L/2).
+ *   lambda   host array of 2^min(cut, L-cut) doubles (descending), or NULL.
+ *   S        host output (may be NULL); eigenvalues <= 0 contribute 0.
+ * The Gram product runs on this library's kernels; the Hermitian eigenvalue
+ * problem is solved by cuSOLVER (heevd), loaded at first use.  Returns
+ * EUNSUPPORTED if cuSOLVER cannot be loaded.  Synchronises.
+ */
+osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, double *lambda,
+                                      double *S);
+
+/*
+ * Timing of the H.psi products with CUDA events recorded on the handle's
+ * stream around every product (all passes), for roofline measurements.
+ * Not from the paper (instrumentation).  enable = 0 stops recording.
+ * osmps_ed_timing_read synchronises the stream and returns the summed device
+ * time in milliseconds and the number of products since the last reset;
+ * reset != 0 clears the counters.
+ */
+osmps_status osmps_ed_timing_enable(osmps_ed_t *ed, int enable);
+osmps_status osmps_ed_timing_read(osmps_ed_t *ed, double *hpsi_ms, int64_t *hpsi_calls, int reset);
+
+/* Number of kernels this handle has launched so far (its own kernels; the
+ * cuSOLVER eigenvalue routine is not counted).  Not from the paper. */
+osmps_status osmps_ed_launch_count(const osmps_ed_t *ed, int64_t *count);
+
+/* Static description of a status code. */
+const char *osmps_ed_strerror(osmps_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSMPS_ED_H */

@@ -1,0 +1,192 @@
+"""GB300-native exact diagonalization of spin-1/2 chains (arXiv:1802.10052 hot path).
+
+Python front end of libosmps_ed: the same calls as the C ABI in
+include/osmps_ed.h, taking torch CUDA tensors (complex128 for ``prec="fp64"``,
+complex64 for ``prec="mixed"``) as state buffers.  PyTorch only provides device
+memory and the CUDA stream; all computation runs in the library's kernels.
+
+    chain = Chain(L=24, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    psi = chain.new_state()
+    chain.init_basis_state(psi, 0)            # all up
+    err = chain.krylov_evolve(psi, dt=0.01, nsteps=10, m=20)
+    sz = chain.measure_local(psi)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from ._binding import (LIB_PATH, OSMPS_ENOCONV, OSMPS_FP64, OSMPS_MIXED, OSMPS_OK, OsmpsError, check, lib)
+
+__all__ = ["Chain", "OsmpsError", "LIB_PATH", "lib"]
+
+_PREC = {"fp64": OSMPS_FP64, "mixed": OSMPS_MIXED}
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Chain:
+    """One chain H = sum_{i<j} J(j-i) sz_i sz_j + sum_k h_k sx_k on the current CUDA device.
+
+    ``couplings`` (length L-1, J(r) for r = 1..L-1) overrides ``J``/``alpha``;
+    ``alpha=None`` means nearest neighbours only.  Signs are taken as given.
+    """
+
+    def __init__(self, L, J=1.0, alpha=None, h=1.0, couplings=None, prec="fp64", stream=None):
+        torch = _torch()
+        self.L = int(L)
+        self.prec = prec
+        self.dtype = torch.complex128 if prec == "fp64" else torch.complex64
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        if couplings is not None:
+            arr = (C.c_double * max(self.L - 1, 1))(*[float(x) for x in couplings])
+            cp = C.cast(arr, C.POINTER(C.c_double))
+        else:
+            cp = None
+        a = -1.0 if alpha is None else float(alpha)
+        handle = C.c_void_p()
+        check(lib.osmps_ed_create(self.L, cp, float(J), a, float(h), _PREC[prec],
+                                  C.c_void_p(self._stream.cuda_stream), C.byref(handle)), "osmps_ed_create")
+        self._h = handle
+
+    # ---- lifetime -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.osmps_ed_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- configuration --------------------------------------------------
+    @property
+    def D(self):
+        return 1 << self.L
+
+    def set_stream(self, stream):
+        self._stream = stream
+        check(lib.osmps_ed_set_stream(self._h, C.c_void_p(stream.cuda_stream)), "osmps_ed_set_stream")
+
+    def set_field(self, h):
+        check(lib.osmps_ed_set_field(self._h, float(h)), "osmps_ed_set_field")
+
+    def set_site_fields(self, h_sites):
+        arr = (C.c_double * self.L)(*[float(x) for x in h_sites])
+        check(lib.osmps_ed_set_site_fields(self._h, arr), "osmps_ed_set_site_fields")
+
+    def set_reorth(self, mode):
+        check(lib.osmps_ed_set_reorth(self._h, int(mode)), "osmps_ed_set_reorth")
+
+    def timing_enable(self, on=True):
+        check(lib.osmps_ed_timing_enable(self._h, 1 if on else 0), "osmps_ed_timing_enable")
+
+    def timing_read(self, reset=True):
+        """(total ms, number of H.psi products) recorded since the last reset."""
+        ms, n = C.c_double(), C.c_int64()
+        check(lib.osmps_ed_timing_read(self._h, C.byref(ms), C.byref(n), 1 if reset else 0), "osmps_ed_timing_read")
+        return ms.value, n.value
+
+    def device_bytes(self):
+        v = C.c_uint64()
+        check(lib.osmps_ed_device_bytes(self._h, C.byref(v)), "osmps_ed_device_bytes")
+        return v.value
+
+    # ---- states ---------------------------------------------------------
+    def new_state(self):
+        torch = _torch()
+        return torch.empty(self.D, dtype=self.dtype, device="cuda")
+
+    def _check_state(self, t):
+        if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous() or t.numel() != self.D:
+            raise ValueError(f"state must be a contiguous CUDA {self.dtype} tensor of {self.D} elements")
+
+    def init_basis_state(self, psi, b):
+        self._check_state(psi)
+        check(lib.osmps_ed_init_basis_state(self._h, _dptr(psi), int(b)), "osmps_ed_init_basis_state")
+
+    def upload(self, dst, src_host):
+        self._check_state(dst)
+        if src_host.dtype != self.dtype or src_host.numel() != self.D or not src_host.is_contiguous():
+            raise ValueError("host buffer has the wrong type or size")
+        check(lib.osmps_ed_upload(self._h, _dptr(dst), C.c_void_p(src_host.data_ptr())), "osmps_ed_upload")
+
+    def download(self, dst_host, src):
+        self._check_state(src)
+        if dst_host.dtype != self.dtype or dst_host.numel() != self.D or not dst_host.is_contiguous():
+            raise ValueError("host buffer has the wrong type or size")
+        check(lib.osmps_ed_download(self._h, C.c_void_p(dst_host.data_ptr()), _dptr(src)), "osmps_ed_download")
+
+    # ---- hot path -------------------------------------------------------
+    def apply_H(self, psi, out):
+        self._check_state(psi)
+        self._check_state(out)
+        check(lib.osmps_ed_apply_H(self._h, _dptr(psi), _dptr(out)), "osmps_ed_apply_H")
+
+    def energy(self, psi):
+        """Returns (<psi|H|psi>, <psi|psi>)."""
+        self._check_state(psi)
+        e, n = C.c_double(), C.c_double()
+        check(lib.osmps_ed_energy(self._h, _dptr(psi), C.byref(e), C.byref(n)), "osmps_ed_energy")
+        return e.value, n.value
+
+    def lanczos_ground(self, psi, tol=1e-12, max_iter=300, raise_on_noconv=True):
+        """In place: psi <- normalised ground state.  Returns (E, residual, iterations)."""
+        self._check_state(psi)
+        e, r, it = C.c_double(), C.c_double(), C.c_int()
+        st = lib.osmps_ed_lanczos_ground(self._h, _dptr(psi), float(tol), int(max_iter), C.byref(e), C.byref(r),
+                                         C.byref(it))
+        allow = (OSMPS_OK,) if raise_on_noconv else (OSMPS_OK, OSMPS_ENOCONV)
+        check(st, "osmps_ed_lanczos_ground", allow)
+        return e.value, r.value, it.value
+
+    def krylov_evolve(self, psi, dt, nsteps, m=20, tol=0.0):
+        """In place: psi <- exp(-i H dt)^nsteps psi.  Returns the summed error estimate."""
+        self._check_state(psi)
+        err = C.c_double()
+        check(lib.osmps_ed_krylov_evolve(self._h, _dptr(psi), float(dt), int(nsteps), int(m), float(tol),
+                                         C.byref(err)), "osmps_ed_krylov_evolve")
+        return err.value
+
+    def measure_local(self, psi):
+        self._check_state(psi)
+        out = np.zeros(self.L)
+        check(lib.osmps_ed_measure_local(self._h, _dptr(psi), out.ctypes.data_as(C.POINTER(C.c_double))),
+              "osmps_ed_measure_local")
+        return out
+
+    def measure_corr(self, psi):
+        self._check_state(psi)
+        out = np.zeros((self.L, self.L))
+        check(lib.osmps_ed_measure_corr(self._h, _dptr(psi), out.ctypes.data_as(C.POINTER(C.c_double))),
+              "osmps_ed_measure_corr")
+        return out
+
+    def schmidt_entropy(self, psi, cut=-1, spectrum=False):
+        """Returns S, or (S, lambda descending) with spectrum=True."""
+        self._check_state(psi)
+        c = self.L // 2 if cut in (-1, None) else int(cut)
+        n = 1 << min(c, self.L - c)
+        lam = np.zeros(n) if spectrum else None
+        S = C.c_double()
+        lp = lam.ctypes.data_as(C.POINTER(C.c_double)) if spectrum else None
+        check(lib.osmps_ed_schmidt_entropy(self._h, _dptr(psi), int(c), lp, C.byref(S)), "osmps_ed_schmidt_entropy")
+        return (S.value, lam) if spectrum else S.value

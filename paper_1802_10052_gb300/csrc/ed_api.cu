@@ -1,0 +1,654 @@
+// C ABI of libosmps_ed (include/osmps_ed.h): argument checks, workspace
+// management and the host-side drivers of the Lanczos and Krylov loops.  The
+// drivers only enqueue kernels; every vector operation and every scalar of the
+// recurrences is computed on the device (see vec_kernels.cu), and the host
+// reads back a few scalars where the ABI returns them.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+
+#include "ed_internal.h"
+
+using namespace osmps;
+
+struct osmps_ed {
+    Handle h;
+    bool reorth_set;
+};
+
+namespace osmps {
+
+void *dev_alloc(Handle *h, size_t bytes, cudaError_t *err) {
+    void *p = nullptr;
+    *err = cudaMalloc(&p, bytes);
+    if (*err != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    h->owned_bytes += bytes;
+    return p;
+}
+
+void dev_free(Handle *h, void *p, size_t bytes) {
+    if (p != nullptr) {
+        cudaFree(p);
+        h->owned_bytes -= bytes;
+    }
+}
+
+}  // namespace osmps
+
+namespace {
+
+osmps_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return OSMPS_OK;
+    if (e == cudaErrorMemoryAllocation) return OSMPS_ENOMEM;
+    return OSMPS_ECUDA;
+}
+
+#define CK(expr)                                  \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) return from_cuda(_e); \
+    } while (0)
+
+#define CKS(expr)                                 \
+    do {                                          \
+        osmps_status _s = (expr);                 \
+        if (_s != OSMPS_OK) return _s;            \
+    } while (0)
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+size_t vec_bytes(const Handle *h) { return (size_t)h->D * h->esize; }
+
+osmps_status ensure_vec(Handle *h, void **p) {
+    if (*p != nullptr) return OSMPS_OK;
+    cudaError_t err;
+    *p = dev_alloc(h, vec_bytes(h), &err);
+    return from_cuda(err);
+}
+
+// V[0] is the caller's state; V[1..nv] are owned Krylov vectors.
+osmps_status ensure_basis(Handle *h, int nv) {
+    if (nv <= h->Vcap) return OSMPS_OK;
+    void **nV = new (std::nothrow) void *[nv + 1];
+    if (nV == nullptr) return OSMPS_ENOMEM;
+    for (int i = 0; i <= nv; ++i) nV[i] = nullptr;
+    for (int i = 1; i <= h->Vcap; ++i) nV[i] = h->V[i];
+    for (int i = h->Vcap + 1; i <= nv; ++i) {
+        cudaError_t err;
+        nV[i] = dev_alloc(h, vec_bytes(h), &err);
+        if (err != cudaSuccess) {
+            for (int k = h->Vcap + 1; k < i; ++k) dev_free(h, nV[k], vec_bytes(h));
+            delete[] nV;
+            return from_cuda(err);
+        }
+    }
+    delete[] h->V;
+    h->V = nV;
+    if (h->V_dev != nullptr) dev_free(h, h->V_dev, sizeof(void *) * (h->Vcap + 1));
+    h->V_dev = nullptr;
+    h->Vcap = nv;
+    cudaError_t err;
+    h->V_dev = (void **)dev_alloc(h, sizeof(void *) * (nv + 1), &err);
+    return from_cuda(err);
+}
+
+osmps_status upload_basis_table(Handle *h, void *psi, int nv) {
+    h->V[0] = psi;
+    CK(cudaMemcpyAsync(h->V_dev, h->V, sizeof(void *) * (nv + 1), cudaMemcpyHostToDevice, h->stream));
+    return OSMPS_OK;
+}
+
+osmps_status read_scalars(Handle *h, size_t off, size_t bytes) {
+    CK(cudaMemcpyAsync(reinterpret_cast<char *>(h->ctl_host) + off, reinterpret_cast<char *>(h->ctl) + off, bytes,
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return OSMPS_OK;
+}
+
+#define CTL_OFF(f) offsetof(KrylovCtl, f)
+
+__global__ void ctl_init_kernel(KrylovCtl *ctl, double bd_tol) {
+    ctl->bd_tol = bd_tol;
+    ctl->err_sum = 0.0;
+    ctl->err = 0.0;
+}
+
+// x = sum y_i v_i was written with partial |x|^2; prepare the residual pass
+// r = H x - theta x on the normalised x
+__global__ void ctl_prepare_residual_kernel(KrylovCtl *ctl, const double *partials, int nparts) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 32) s += partials[4 * (size_t)i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) {
+        const double n = sqrt(s);
+        ctl->work[0] = (n > 0.0) ? 1.0 / n : 0.0;  // scale applied to x
+        ctl->epi2[0] = 1.0;
+        ctl->epi2[1] = ctl->theta;
+        ctl->epi2[2] = 0.0;
+    }
+}
+
+// residual pass reduced: work[1] = ||H x - theta x||, work[2] = <x, H x> = theta + <x, r>
+__global__ void ctl_finish_residual_kernel(KrylovCtl *ctl, const double *partials, int nparts) {
+    double d = 0.0, n2 = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 32) {
+        d += partials[4 * (size_t)i];
+        n2 += partials[4 * (size_t)i + 2];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        d += __shfl_xor_sync(0xffffffffu, d, off);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+    }
+    if (threadIdx.x == 0) {
+        ctl->work[1] = sqrt(n2);
+        ctl->work[2] = ctl->theta + d;
+    }
+}
+
+// energy pass reduced: work[3] = <u, H u>, work[4] = <u, u>
+__global__ void ctl_finish_energy_kernel(KrylovCtl *ctl, const double *partials, int nparts) {
+    double d = 0.0, n2 = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 32) {
+        d += partials[4 * (size_t)i];
+        n2 += partials[4 * (size_t)i + 2];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        d += __shfl_xor_sync(0xffffffffu, d, off);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+    }
+    if (threadIdx.x == 0) {
+        ctl->work[3] = d;
+        ctl->work[4] = n2;
+    }
+}
+
+// One Lanczos iteration j: w = H v_j - beta_j v_{j-1} (fused), alpha_j,
+// u_{j+1} = w - alpha_j v_j, optional Gram-Schmidt against v_0..v_j, beta_{j+1}.
+osmps_status lanczos_iteration(Handle *h, int j, int reorth) {
+    int np = 0;
+    HpsiArgs a{};
+    a.u = h->V[j];
+    a.uprev = j > 0 ? h->V[j - 1] : nullptr;
+    a.out = h->V[j + 1];
+    a.tmp = h->tmp;
+    a.epi = h->ctl->epi;
+    a.partials = h->partials;
+    a.m_eff = &h->ctl->m_eff;
+    a.stop_index = j;
+    a.epilogue = EPI_KRYLOV;
+    CK(launch_hpsi_timed(h, a, &np));
+    CK(launch_ctl_after_hpsi(h, h->ctl, h->partials, np, j));
+    CK(launch_update(h, h->V[j + 1], h->V[j], h->ctl, j, h->partials, &np));
+    if (reorth) {
+        int nd = 0;
+        CK(launch_multidot(h, h->V_dev, j + 1, h->V[j + 1], h->ctl, j, h->partials2, &nd));
+        CK(launch_reorth_update(h, h->V_dev, j + 1, h->V[j + 1], h->ctl, j, h->partials2, nd, h->partials, &np));
+    }
+    CK(launch_ctl_after_update(h, h->ctl, h->partials, np, j, 0));
+    return OSMPS_OK;
+}
+
+osmps_status check_state_ptr(const Handle *h, const void *p) {
+    (void)h;
+    if (p == nullptr || !aligned16(p)) return OSMPS_EINVAL;
+    return OSMPS_OK;
+}
+
+osmps_status timing_flush(Handle *h) {
+    if (h->tev_used == 0) return OSMPS_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < h->tev_used; ++i) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, h->tev[2 * i], h->tev[2 * i + 1]));
+        h->t_ms += ms;
+    }
+    h->t_calls += h->tev_used;
+    h->tev_used = 0;
+    return OSMPS_OK;
+}
+
+void destroy_handle(Handle *h) {
+    cudaStreamSynchronize(h->stream);
+    if (h->tev) {
+        for (int i = 0; i < 2 * h->tev_cap; ++i) cudaEventDestroy(h->tev[i]);
+        delete[] h->tev;
+    }
+    dev_free(h, h->Ell, 0);
+    dev_free(h, h->Fhh, 0);
+    dev_free(h, h->partials, 0);
+    dev_free(h, h->partials2, 0);
+    dev_free(h, h->dscratch, 0);
+    dev_free(h, h->ctl, 0);
+    if (h->ctl_host) cudaFreeHost(h->ctl_host);
+    dev_free(h, h->tmp, 0);
+    dev_free(h, h->xbuf, 0);
+    if (h->V) {
+        for (int i = 1; i <= h->Vcap; ++i) dev_free(h, h->V[i], 0);
+        delete[] h->V;
+    }
+    dev_free(h, h->V_dev, 0);
+    dev_free(h, h->gram, 0);
+    dev_free(h, h->solver_ws, 0);
+    dev_free(h, h->lam_dev, 0);
+}
+
+}  // namespace
+
+namespace osmps {
+
+cudaError_t launch_hpsi_timed(Handle *h, const HpsiArgs &a, int *nparts_out) {
+    if (!h->timing) return launch_hpsi(h, a, nparts_out);
+    if (h->tev_used == h->tev_cap) {
+        // flush recorded pairs when the pool is full, then reuse it
+        if (h->tev_cap >= 4096) {
+            if (timing_flush(h) != OSMPS_OK) return cudaErrorUnknown;
+        } else {
+            const int ncap = h->tev_cap ? 2 * h->tev_cap : 256;
+            cudaEvent_t *nev = new (std::nothrow) cudaEvent_t[2 * ncap];
+            if (nev == nullptr) return cudaErrorMemoryAllocation;
+            for (int i = 0; i < 2 * h->tev_cap; ++i) nev[i] = h->tev[i];
+            for (int i = 2 * h->tev_cap; i < 2 * ncap; ++i) {
+                cudaError_t e = cudaEventCreate(&nev[i]);
+                if (e != cudaSuccess) return e;
+            }
+            delete[] h->tev;
+            h->tev = nev;
+            h->tev_cap = ncap;
+        }
+    }
+    const int i = h->tev_used++;
+    cudaError_t e = cudaEventRecord(h->tev[2 * i], h->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_hpsi(h, a, nparts_out);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(h->tev[2 * i + 1], h->stream);
+}
+
+}  // namespace osmps
+
+extern "C" {
+
+osmps_status osmps_ed_launch_count(const osmps_ed_t *ed, int64_t *count) {
+    if (ed == nullptr || count == nullptr) return OSMPS_EINVAL;
+    *count = ed->h.launches;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_timing_enable(osmps_ed_t *ed, int enable) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    ed->h.timing = enable ? 1 : 0;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_timing_read(osmps_ed_t *ed, double *hpsi_ms, int64_t *hpsi_calls, int reset) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    CKS(timing_flush(&ed->h));
+    if (hpsi_ms) *hpsi_ms = ed->h.t_ms;
+    if (hpsi_calls) *hpsi_calls = ed->h.t_calls;
+    if (reset) {
+        ed->h.t_ms = 0.0;
+        ed->h.t_calls = 0;
+    }
+    return OSMPS_OK;
+}
+
+const char *osmps_ed_strerror(osmps_status s) {
+    switch (s) {
+        case OSMPS_OK: return "success";
+        case OSMPS_EINVAL: return "invalid argument";
+        case OSMPS_ENOMEM: return "out of memory";
+        case OSMPS_ECUDA: return "CUDA error";
+        case OSMPS_ENOCONV: return "no convergence within max_iter";
+        case OSMPS_ETIMEOUT: return "bounded device wait timed out";
+        case OSMPS_EUNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+osmps_status osmps_ed_create(int L, const double *couplings, double J, double alpha, double h, int prec,
+                             void *cuda_stream, osmps_ed_t **out) {
+    if (out == nullptr) return OSMPS_EINVAL;
+    *out = nullptr;
+    if (L < 1 || L > OSMPS_MAX_L) return OSMPS_EINVAL;
+    if (prec != OSMPS_FP64 && prec != OSMPS_MIXED) return OSMPS_EINVAL;
+    if (!std::isfinite(h)) return OSMPS_EINVAL;
+    double Jr[kMaxL + 1] = {0};
+    if (couplings != nullptr) {
+        for (int r = 1; r < L; ++r) {
+            if (!std::isfinite(couplings[r - 1])) return OSMPS_EINVAL;
+            Jr[r] = couplings[r - 1];
+        }
+    } else {
+        if (!std::isfinite(J) || std::isnan(alpha)) return OSMPS_EINVAL;
+        const bool nn = (alpha < 0.0) || std::isinf(alpha);
+        for (int r = 1; r < L; ++r) Jr[r] = nn ? (r == 1 ? J : 0.0) : J / std::pow((double)r, alpha);
+    }
+    osmps_ed_t *ed = new (std::nothrow) osmps_ed_t();
+    if (ed == nullptr) return OSMPS_ENOMEM;
+    std::memset(&ed->h, 0, sizeof(Handle));
+    ed->reorth_set = false;
+    Handle *hd = &ed->h;
+    hd->L = L;
+    hd->prec = prec;
+    hd->D = 1ull << L;
+    hd->esize = (prec == OSMPS_FP64) ? 16 : 8;
+    hd->stream = (cudaStream_t)cuda_stream;
+    for (int r = 0; r <= kMaxL; ++r) hd->Jr[r] = Jr[r];
+    for (int b = 0; b < L; ++b) hd->hbit[b] = h;
+    hd->reorth = 0;
+    cudaError_t err = cudaGetDevice(&hd->device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&hd->nsm, cudaDevAttrMultiProcessorCount, hd->device);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        delete ed;
+        return from_cuda(err);
+    }
+    hd->plan = make_plan(L, prec);
+    osmps_status st = OSMPS_OK;
+    do {
+        err = build_tables(hd);
+        if (err != cudaSuccess) break;
+        // per-CTA partials: 4 doubles per CTA for every streaming kernel; the
+        // multi-dot of the Gram-Schmidt pass needs 2 per vector per CTA
+        const size_t g = (size_t)hd->nsm * 8;
+        hd->partials_cap = g * 4;
+        hd->partials = (double *)dev_alloc(hd, sizeof(double) * hd->partials_cap, &err);
+        if (err != cudaSuccess) break;
+        const size_t zneed = g * ((size_t)(L * L + L + 1) + 1024);
+        const size_t dneed = g * 2 * (kMaxLanczos + 1);
+        hd->partials2_cap = zneed > dneed ? zneed : dneed;
+        hd->partials2 = (double *)dev_alloc(hd, sizeof(double) * hd->partials2_cap, &err);
+        if (err != cudaSuccess) break;
+        hd->dscratch_cap = (size_t)L * L + L + 64;
+        hd->dscratch = (double *)dev_alloc(hd, sizeof(double) * hd->dscratch_cap, &err);
+        if (err != cudaSuccess) break;
+        hd->ctl = (KrylovCtl *)dev_alloc(hd, sizeof(KrylovCtl), &err);
+        if (err != cudaSuccess) break;
+        err = cudaMallocHost(&hd->ctl_host, sizeof(KrylovCtl));
+        if (err != cudaSuccess) break;
+        err = cudaMemsetAsync(hd->ctl, 0, sizeof(KrylovCtl), hd->stream);
+        if (err != cudaSuccess) break;
+        if (hd->plan.npass > 1) {
+            hd->tmp = dev_alloc(hd, vec_bytes(hd), &err);
+            if (err != cudaSuccess) break;
+        }
+        err = cudaStreamSynchronize(hd->stream);
+    } while (0);
+    if (err != cudaSuccess) st = from_cuda(err);
+    if (st != OSMPS_OK) {
+        destroy_handle(hd);
+        delete ed;
+        return st;
+    }
+    *out = ed;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_destroy(osmps_ed_t *ed) {
+    if (ed == nullptr) return OSMPS_OK;
+    destroy_handle(&ed->h);
+    delete ed;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_stream(osmps_ed_t *ed, void *cuda_stream) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    ed->h.stream = (cudaStream_t)cuda_stream;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_field(osmps_ed_t *ed, double h) {
+    if (ed == nullptr || !std::isfinite(h)) return OSMPS_EINVAL;
+    for (int b = 0; b < ed->h.L; ++b) ed->h.hbit[b] = h;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_site_fields(osmps_ed_t *ed, const double *h_sites) {
+    if (ed == nullptr || h_sites == nullptr) return OSMPS_EINVAL;
+    const int L = ed->h.L;
+    for (int k = 0; k < L; ++k)
+        if (!std::isfinite(h_sites[k])) return OSMPS_EINVAL;
+    for (int k = 1; k <= L; ++k) ed->h.hbit[L - k] = h_sites[k - 1];
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_reorth(osmps_ed_t *ed, int mode) {
+    if (ed == nullptr || (mode != 0 && mode != 1)) return OSMPS_EINVAL;
+    ed->h.reorth = mode;
+    ed->reorth_set = true;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_dim(const osmps_ed_t *ed, uint64_t *D) {
+    if (ed == nullptr || D == nullptr) return OSMPS_EINVAL;
+    *D = ed->h.D;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_device_bytes(const osmps_ed_t *ed, uint64_t *bytes) {
+    if (ed == nullptr || bytes == nullptr) return OSMPS_EINVAL;
+    *bytes = ed->h.owned_bytes;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_init_basis_state(osmps_ed_t *ed, void *psi, uint64_t b) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    CKS(check_state_ptr(&ed->h, psi));
+    if (b >= ed->h.D) return OSMPS_EINVAL;
+    CK(launch_fill_basis(&ed->h, psi, b));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_upload(osmps_ed_t *ed, void *dst_device, const void *src_host) {
+    if (ed == nullptr || src_host == nullptr) return OSMPS_EINVAL;
+    CKS(check_state_ptr(&ed->h, dst_device));
+    CK(cudaMemcpyAsync(dst_device, src_host, vec_bytes(&ed->h), cudaMemcpyHostToDevice, ed->h.stream));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_download(osmps_ed_t *ed, void *dst_host, const void *src_device) {
+    if (ed == nullptr || dst_host == nullptr) return OSMPS_EINVAL;
+    CKS(check_state_ptr(&ed->h, src_device));
+    CK(cudaMemcpyAsync(dst_host, src_device, vec_bytes(&ed->h), cudaMemcpyDeviceToHost, ed->h.stream));
+    CK(cudaStreamSynchronize(ed->h.stream));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_apply_H(osmps_ed_t *ed, const void *psi, void *out) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    CKS(check_state_ptr(h, out));
+    if (psi == out) return OSMPS_EINVAL;
+    HpsiArgs a{};
+    a.u = psi;
+    a.out = out;
+    a.tmp = h->tmp;
+    a.epilogue = EPI_PLAIN;
+    CK(launch_hpsi_timed(h, a, nullptr));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_energy(osmps_ed_t *ed, const void *psi, double *e_num, double *norm2) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    CKS(ensure_vec(h, &h->xbuf));
+    int np = 0;
+    HpsiArgs a{};
+    a.u = psi;
+    a.out = h->xbuf;
+    a.tmp = h->tmp;
+    a.partials = h->partials;
+    a.epilogue = EPI_ENERGY;
+    CK(launch_hpsi_timed(h, a, &np));
+    ctl_finish_energy_kernel<<<1, 32, 0, h->stream>>>(h->ctl, h->partials, np);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    CKS(read_scalars(h, CTL_OFF(work) + 3 * sizeof(double), 2 * sizeof(double)));
+    if (e_num) *e_num = h->ctl_host->work[3];
+    if (norm2) *norm2 = h->ctl_host->work[4];
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_krylov_evolve(osmps_ed_t *ed, void *psi, double dt, int nsteps, int m, double tol,
+                                    double *err_estimate) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    if (!std::isfinite(dt) || nsteps < 0 || m < 1 || m > kMaxKrylov || std::isnan(tol)) return OSMPS_EINVAL;
+    if (nsteps == 0) {
+        if (err_estimate) *err_estimate = 0.0;
+        return OSMPS_OK;
+    }
+    CKS(ensure_basis(h, m));
+    CKS(upload_basis_table(h, psi, m));
+    ctl_init_kernel<<<1, 1, 0, h->stream>>>(h->ctl, tol > 0.0 ? tol : 1e-12);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    int np = 0;
+    CK(launch_norm2(h, psi, h->partials, &np));
+    CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, m));
+    for (int s = 0; s < nsteps; ++s) {
+        for (int j = 0; j < m; ++j) CKS(lanczos_iteration(h, j, h->reorth));
+        CK(launch_tridiag_exp(h, h->ctl, m, dt));
+        CK(launch_combine(h, h->V_dev, m, psi, h->ctl, h->partials, &np));
+        CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, m));
+    }
+    CKS(read_scalars(h, CTL_OFF(err_sum), sizeof(double)));
+    if (err_estimate) *err_estimate = h->ctl_host->err_sum;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_lanczos_ground(osmps_ed_t *ed, void *psi, double tol, int max_iter, double *energy,
+                                     double *residual, int *iters) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1 || max_iter > kMaxLanczos) return OSMPS_EINVAL;
+    const int reorth = ed->reorth_set ? h->reorth : 1;
+    CKS(ensure_basis(h, max_iter));
+    CKS(ensure_vec(h, &h->xbuf));
+    void *rbuf = h->V[max_iter];  // scratch for the residual vector (last slot)
+    CKS(upload_basis_table(h, psi, max_iter));
+    ctl_init_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 1e-14);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    int np = 0;
+    CK(launch_norm2(h, psi, h->partials, &np));
+    CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, max_iter));
+    double best_res = INFINITY, best_e = NAN;
+    int done_iters = 0;
+    osmps_status result = OSMPS_ENOCONV;
+    for (int j = 0; j < max_iter - 1; ++j) {
+        CKS(lanczos_iteration(h, j, reorth));
+        done_iters = j + 1;
+        CK(launch_tridiag_ground(h, h->ctl, j + 1));
+        CKS(read_scalars(h, CTL_OFF(theta), CTL_OFF(m_eff) + sizeof(int) - CTL_OFF(theta)));
+        const bool breakdown = h->ctl_host->m_eff <= j + 1;
+        const bool last = (j == max_iter - 2);
+        if (!(h->ctl_host->est <= tol) && !breakdown && !last) continue;
+        // Ritz vector x = sum y_i v_i (into xbuf), normalised; explicit residual
+        CK(launch_combine(h, h->V_dev, j + 1, h->xbuf, h->ctl, h->partials, &np));
+        ctl_prepare_residual_kernel<<<1, 32, 0, h->stream>>>(h->ctl, h->partials, np);
+    h->launches += 1;
+        CK(cudaGetLastError());
+        CK(launch_scale(h, h->xbuf, &h->ctl->work[0]));
+        HpsiArgs a{};
+        a.u = h->xbuf;
+        a.out = rbuf;
+        a.tmp = h->tmp;
+        a.epi = h->ctl->epi2;
+        a.partials = h->partials;
+        a.epilogue = EPI_KRYLOV;
+        CK(launch_hpsi_timed(h, a, &np));
+        ctl_finish_residual_kernel<<<1, 32, 0, h->stream>>>(h->ctl, h->partials, np);
+    h->launches += 1;
+        CK(cudaGetLastError());
+        CKS(read_scalars(h, CTL_OFF(work), 3 * sizeof(double)));
+        const double res = h->ctl_host->work[1];
+        const double e = h->ctl_host->work[2];
+        if (res < best_res) {
+            best_res = res;
+            best_e = e;
+            CK(cudaMemcpyAsync(psi, h->xbuf, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+        }
+        if (res <= tol) {
+            result = OSMPS_OK;
+            break;
+        }
+        if (breakdown) break;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (energy) *energy = best_e;
+    if (residual) *residual = best_res;
+    if (iters) *iters = done_iters;
+    return result;
+}
+
+osmps_status osmps_ed_measure_local(osmps_ed_t *ed, const void *psi, double *sz) {
+    if (ed == nullptr || sz == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    CK(launch_zstats(h, psi, h->dscratch));
+    CK(cudaMemcpyAsync(sz, h->dscratch, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_measure_corr(osmps_ed_t *ed, const void *psi, double *szsz) {
+    if (ed == nullptr || szsz == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    CK(launch_zstats(h, psi, h->dscratch));
+    CK(cudaMemcpyAsync(szsz, h->dscratch + h->L, sizeof(double) * h->L * h->L, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, double *lambda, double *S) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    const int L = h->L;
+    if (cut == -1) cut = L / 2;
+    if (L < 2 || cut < 1 || cut > L - 1) return OSMPS_EINVAL;
+    const int ls = cut < L - cut ? cut : L - cut;
+    const int n = 1 << ls;
+    const size_t gbytes = (size_t)n * n * h->esize;
+    if (gbytes > h->gram_bytes) {
+        dev_free(h, h->gram, h->gram_bytes);
+        h->gram = nullptr;
+        h->gram_bytes = 0;
+        cudaError_t err;
+        h->gram = dev_alloc(h, gbytes, &err);
+        if (err != cudaSuccess) return from_cuda(err);
+        h->gram_bytes = gbytes;
+    }
+    if ((size_t)n + 1 > h->lam_cap) {
+        dev_free(h, h->lam_dev, h->lam_cap * sizeof(double));
+        h->lam_dev = nullptr;
+        h->lam_cap = 0;
+        cudaError_t err;
+        h->lam_dev = (double *)dev_alloc(h, sizeof(double) * (n + 1), &err);
+        if (err != cudaSuccess) return from_cuda(err);
+        h->lam_cap = n + 1;
+    }
+    int nn = 0;
+    CK(launch_gram(h, psi, cut, h->gram, &nn));
+    CKS(schmidt_eig(h, h->gram, nn, h->lam_dev, h->lam_dev + nn));
+    if (lambda) CK(cudaMemcpyAsync(lambda, h->lam_dev, sizeof(double) * nn, cudaMemcpyDeviceToHost, h->stream));
+    double Sv = 0.0;
+    CK(cudaMemcpyAsync(&Sv, h->lam_dev + nn, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (S) *S = Sv;
+    return OSMPS_OK;
+}
+
+}  // extern "C"

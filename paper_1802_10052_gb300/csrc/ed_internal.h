@@ -1,0 +1,165 @@
+// Internal declarations shared by the translation units of libosmps_ed.
+// Not part of the public ABI (include/osmps_ed.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/osmps_ed.h"
+
+namespace osmps {
+
+// ---------------------------------------------------------------------------
+// Limits and tiling constants
+// ---------------------------------------------------------------------------
+constexpr int kMaxL = OSMPS_MAX_L;
+constexpr int kMaxKrylov = 64;       // vectors per Krylov step
+constexpr int kMaxLanczos = 1000;    // Lanczos vectors
+constexpr int kPassThreads = 512;    // threads per CTA of the H.psi passes
+constexpr int kVecThreads = 256;     // threads per CTA of the streaming vector kernels
+constexpr int kTileBytesLog2 = 16;   // 64 KiB shared-memory tile per H.psi CTA
+constexpr int kChunkBytesLog2 = 7;   // 128-byte contiguous chunks in the strided passes
+constexpr int kMaxPasses = 4;
+
+// Scalars the device-side Krylov/Lanczos control kernels keep between launches.
+struct KrylovCtl {
+    double alpha[kMaxLanczos];        // T diagonal
+    double beta[kMaxLanczos + 1];     // T off-diagonal, beta[j] couples j-1 and j
+    double scale[kMaxLanczos + 1];    // v_j = scale[j] * u_j (stored vectors unnormalised)
+    double coef_re[kMaxLanczos];      // combination coefficients (already times scale)
+    double coef_im[kMaxLanczos];
+    double nrm;                       // ||psi|| at the start of the step
+    double err;                       // a-posteriori error estimate of the step
+    double err_sum;                   // summed over steps
+    double theta;                     // lowest Ritz value (ground state)
+    double est;                       // beta_{j+1} |y_j| (ground state)
+    double epi[3];                    // epilogue scalars of the next H.psi: sv, a, b
+    double epi2[3];                   // epilogue scalars of the ground-state residual pass
+    double bd_tol;                    // relative breakdown threshold
+    int m_eff;                        // vectors in the basis (< m after breakdown)
+    int pad;
+    double work[7 * kMaxLanczos];     // scratch of the single-thread tridiagonal solves
+};
+
+// One pass of the multi-pass H.psi (see hpsi_kernels.cu for the scheme).
+struct PassDesc {
+    int c;        // contiguous chunk bits carried but not flipped
+    int o;        // first global bit of the flipped group
+    int g;        // number of flipped bits
+    int first;    // computes the diagonal and writes (no accumulate input)
+    long long ntiles;
+};
+
+struct PassPlan {
+    int npass;
+    int a1;       // bits of the first (contiguous) pass
+    int ta;       // split of a1 for the per-tile diagonal tables
+    PassDesc p[kMaxPasses];
+};
+
+// Epilogue of the last pass.
+enum Epilogue : int {
+    EPI_PLAIN = 0,   // out = H u
+    EPI_KRYLOV = 1,  // out = sv*H u - a*sv*u - b*uprev; partials <sv u, out>, |out|^2
+    EPI_ENERGY = 2   // no write; partials <u, H u>, |u|^2
+};
+
+struct HpsiArgs {
+    const void *u;
+    const void *uprev;
+    void *out;
+    void *tmp;                 // partial-sum vector between passes
+    const double *epi;         // device epilogue scalars (sv, a, b) or nullptr (=1,0,0)
+    double *partials;          // per-CTA partial sums, 4 doubles per CTA
+    const int *m_eff;          // skip the launch when *m_eff <= stop_index
+    int stop_index;
+    int epilogue;
+};
+
+struct Handle;
+
+// hpsi_kernels.cu
+PassPlan make_plan(int L, int prec);
+cudaError_t build_tables(Handle *h);
+cudaError_t launch_hpsi(Handle *h, const HpsiArgs &a, int *nparts_out);
+cudaError_t launch_hpsi_timed(Handle *h, const HpsiArgs &a, int *nparts_out);
+int hpsi_grid(Handle *h, int pass);
+
+// vec_kernels.cu
+cudaError_t launch_fill_basis(Handle *h, void *psi, uint64_t b);
+cudaError_t launch_norm2(Handle *h, const void *x, double *partials, int *nparts);
+cudaError_t launch_ctl_after_norm(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j);
+cudaError_t launch_ctl_after_hpsi(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j);
+cudaError_t launch_update(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, double *partials,
+                          int *nparts);
+cudaError_t launch_ctl_after_update(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j,
+                                    int mode);
+cudaError_t launch_multidot(Handle *h, void *const *V, int nvec, const void *w, KrylovCtl *ctl, int j,
+                            double *partials, int *nparts);   // 2*nvec doubles per CTA
+cudaError_t launch_reorth_update(Handle *h, void *const *V, int nvec, void *w, KrylovCtl *ctl, int j,
+                                 const double *dots, int ndots_parts, double *partials, int *nparts);
+cudaError_t launch_tridiag_exp(Handle *h, KrylovCtl *ctl, int m, double dt);
+cudaError_t launch_tridiag_ground(Handle *h, KrylovCtl *ctl, int m);
+cudaError_t launch_combine(Handle *h, void *const *V, int nvec, void *out, KrylovCtl *ctl, double *partials,
+                           int *nparts);
+cudaError_t launch_scale(Handle *h, void *x, const double *s_dev);
+int vec_grid(Handle *h);
+
+// measure_kernels.cu
+cudaError_t launch_zstats(Handle *h, const void *psi, double *out_dev);
+cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_out);
+osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev);
+
+// Device memory owned by a handle.
+struct Handle {
+    int L;
+    int prec;                   // OSMPS_FP64 / OSMPS_MIXED
+    uint64_t D;
+    size_t esize;               // bytes per amplitude (16 or 8)
+    cudaStream_t stream;
+    int device;
+    int nsm;
+    double Jr[kMaxL + 1];       // J(r), index r (J[0] unused)
+    double hbit[kMaxL + 1];     // field on bit b (site L-b)
+    int reorth;
+    PassPlan plan;
+
+    // tables for the diagonal energy
+    void *Ell;                  // 2^a1 entries (T)
+    void *Fhh;                  // 2^(L-a1) x (a1+1) entries (T)
+
+    // scratch
+    double *partials;           // per-CTA partial sums
+    size_t partials_cap;        // doubles
+    double *partials2;
+    size_t partials2_cap;
+    double *dscratch;           // small FP64 device scratch (outputs before D2H)
+    size_t dscratch_cap;
+    KrylovCtl *ctl;             // device control block
+    KrylovCtl *ctl_host;        // pinned host mirror (scalars read back)
+    void *tmp;                  // pass-to-pass partial vector (D elements)
+    void *xbuf;                 // Ritz vector of the ground state (D elements)
+    void **V;                   // host array of Krylov vector pointers (V[0] = caller psi)
+    void **V_dev;               // device copy of the pointer table
+    int Vcap;                   // allocated vectors (excluding V[0])
+    void *gram;                 // Gram matrix buffer
+    size_t gram_bytes;
+    void *solver_ws;            // cuSOLVER workspace
+    size_t solver_ws_bytes;
+    double *lam_dev;
+    size_t lam_cap;
+    uint64_t owned_bytes;
+    // optional event timing of the H.psi products
+    int timing;
+    cudaEvent_t *tev;           // pairs (start, stop)
+    int tev_cap;                // pairs allocated
+    int tev_used;               // pairs recorded since the last read
+    double t_ms;                // accumulated at read time
+    int64_t t_calls;
+    int64_t launches;           // kernels this handle has launched
+};
+
+void *dev_alloc(Handle *h, size_t bytes, cudaError_t *err);
+void dev_free(Handle *h, void *p, size_t bytes);
+
+}  // namespace osmps

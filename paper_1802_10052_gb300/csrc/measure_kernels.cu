@@ -1,0 +1,385 @@
+// Measurements of a pure state (Sec. IV):
+//   * <sz_k> and <sz_i sz_j> from p_b = |psi_b|^2 in one streaming pass,
+//   * the half-chain reduced density matrix rho = M M^dagger (bond entropy)
+//     and its spectrum, S = -sum_j Lambda_j ln Lambda_j.
+//
+// Correlators: with b = (hi, lo) split at t low bits, per tile of fixed hi the
+// CTA forms P(hi) = sum_lo p and M_j(hi) = sum_lo s_j(lo) p (j < t).  Then
+//   <sz_i sz_i'> (both high) = sum_hi s_i s_i' P,   <sz_i sz_j> = sum_hi s_i M_j,
+//   <sz_j sz_j'> (both low)  = sum_lo s_j s_j' G(lo),  G(lo) = sum_hi p(hi, lo),
+// so every amplitude costs O(1) FP64 work while the L^2 outputs are updated
+// once per tile.  All sums are FP64 in a fixed order.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+#include <dlfcn.h>
+#include <math.h>
+
+#include "ed_internal.h"
+
+namespace osmps {
+
+constexpr int kZThreads = 256;
+constexpr int kZTileBits = 10;
+
+template <typename T> struct ZV;
+template <> struct ZV<float> {
+    typedef float2 c;
+};
+template <> struct ZV<double> {
+    typedef double2 c;
+};
+
+// number of per-CTA accumulators: C (L*L) + m (L) + total
+__host__ __device__ inline int zacc_count(int L) { return L * L + L + 1; }
+
+template <typename T>
+__global__ void __launch_bounds__(kZThreads) zstats_kernel(const typename ZV<T>::c *psi, int L, int t,
+                                                           long long ntiles, double *blockacc, double *Gpart) {
+    const int nel = 1 << t;
+    const int per = (nel + kZThreads - 1) / kZThreads;   // elements per thread (<= 4)
+    const int nacc = zacc_count(L);
+    const int nown = (nacc + kZThreads - 1) / kZThreads; // accumulators per thread (<= 4 for L <= 30)
+    double own[4] = {0, 0, 0, 0};
+    double G[4] = {0, 0, 0, 0};
+    __shared__ double red[kZTileBits + 1][kZThreads / 32];
+    __shared__ double stat[kZTileBits + 1];  // P, M_0..M_{t-1}
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t base = (uint64_t)tile << t;
+        double v[kZTileBits + 1];
+#pragma unroll
+        for (int j = 0; j <= kZTileBits; ++j) v[j] = 0.0;
+        double Pt = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < per) {
+                const int li = threadIdx.x + k * kZThreads;
+                if (li < nel) {
+                    const typename ZV<T>::c a = psi[base + li];
+                    const double p = (double)(a.x * a.x + a.y * a.y);
+                    G[k] += p;
+                    Pt += p;
+                    // bits of li above the thread index
+                    for (int j = 8; j < t; ++j) v[1 + j] += ((li >> j) & 1) ? -p : p;
+                }
+            }
+        }
+        v[0] = Pt;
+        for (int j = 0; j < t && j < 8; ++j) v[1 + j] = ((threadIdx.x >> j) & 1) ? -Pt : Pt;
+        // block reduction of t+1 values
+        for (int j = 0; j <= t; ++j) {
+            double s = v[j];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x <= t) {
+            double s = 0.0;
+            for (int w = 0; w < kZThreads / 32; ++w) s += red[threadIdx.x][w];
+            stat[threadIdx.x] = s;
+        }
+        __syncthreads();
+        const double P = stat[0];
+        // per-CTA accumulators
+        for (int k = 0; k < nown; ++k) {
+            const int e = threadIdx.x + k * kZThreads;
+            if (e >= nacc) break;
+            double add = 0.0;
+            if (e < L * L) {
+                const int i = e / L, j = e % L;  // bit indices
+                if (i >= t && j >= t) {
+                    const int si = 1 - 2 * (int)((tile >> (i - t)) & 1);
+                    const int sj = 1 - 2 * (int)((tile >> (j - t)) & 1);
+                    add = (double)(si * sj) * P;
+                } else if (i >= t && j < t) {
+                    const int si = 1 - 2 * (int)((tile >> (i - t)) & 1);
+                    add = (double)si * stat[1 + j];
+                } else if (i < t && j >= t) {
+                    const int sj = 1 - 2 * (int)((tile >> (j - t)) & 1);
+                    add = (double)sj * stat[1 + i];
+                }
+            } else if (e < L * L + L) {
+                const int i = e - L * L;
+                if (i >= t) {
+                    const int si = 1 - 2 * (int)((tile >> (i - t)) & 1);
+                    add = (double)si * P;
+                } else {
+                    add = stat[1 + i];
+                }
+            } else {
+                add = P;
+            }
+            own[k] += add;
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < nown; ++k) {
+        const int e = threadIdx.x + k * kZThreads;
+        if (e < nacc) blockacc[(size_t)blockIdx.x * nacc + e] = own[k];
+    }
+    for (int k = 0; k < per; ++k) {
+        const int li = threadIdx.x + k * kZThreads;
+        if (li < nel) Gpart[(size_t)blockIdx.x * nel + li] = G[k];
+    }
+}
+
+// Sum the per-CTA partials (fixed order) and assemble the outputs in site order:
+// out[0..L) = <sz_k>, out[L..L+L*L) = <sz_i sz_j>.
+__global__ void zstats_finalize_kernel(const double *blockacc, const double *Gpart, int nblk, int L, int t,
+                                       double *out) {
+    const int nacc = zacc_count(L);
+    const int nel = 1 << t;
+    extern __shared__ double Gs[];
+    for (int li = threadIdx.x; li < nel; li += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += Gpart[(size_t)b * nel + li];
+        Gs[li] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < L + L * L; e += blockDim.x) {
+        double s = 0.0;
+        if (e < L) {
+            const int site = e + 1, bit = L - site;
+            for (int b = 0; b < nblk; ++b) s += blockacc[(size_t)b * nacc + L * L + bit];
+        } else {
+            const int q = e - L;
+            const int si = q / L + 1, sj = q % L + 1;
+            const int bi = L - si, bj = L - sj;
+            if (bi == bj) {
+                for (int b = 0; b < nblk; ++b) s += blockacc[(size_t)b * nacc + L * L + L];
+            } else if (bi < t && bj < t) {
+                for (int lo = 0; lo < nel; ++lo) {
+                    const int sg = (((lo >> bi) ^ (lo >> bj)) & 1) ? -1 : 1;
+                    s += (double)sg * Gs[lo];
+                }
+            } else {
+                for (int b = 0; b < nblk; ++b) s += blockacc[(size_t)b * nacc + bi * L + bj];
+            }
+        }
+        out[e] = s;
+    }
+}
+
+template <typename T>
+static cudaError_t zstats_t(Handle *h, const void *psi, double *out_dev) {
+    const int L = h->L;
+    const int t = L < kZTileBits ? L : kZTileBits;
+    const long long ntiles = 1ll << (L - t);
+    long long cap = (long long)h->nsm * 4;
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    const size_t need = (size_t)grid * (zacc_count(L) + (1u << t));
+    if (need > h->partials2_cap) return cudaErrorMemoryAllocation;
+    double *blockacc = h->partials2;
+    double *Gpart = h->partials2 + (size_t)grid * zacc_count(L);
+    zstats_kernel<T><<<grid, kZThreads, 0, h->stream>>>(reinterpret_cast<const typename ZV<T>::c *>(psi), L, t,
+                                                         ntiles, blockacc, Gpart);
+    zstats_finalize_kernel<<<1, 512, sizeof(double) << t, h->stream>>>(blockacc, Gpart, grid, L, t, out_dev);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zstats(Handle *h, const void *psi, double *out_dev) {
+    return h->prec == OSMPS_FP64 ? zstats_t<double>(h, psi, out_dev) : zstats_t<float>(h, psi, out_dev);
+}
+
+// ---------------------------------------------------------------------------
+// Gram product rho[x][y] = sum_k A[x,k] conj(A[y,k]),  A[x,k] = psi[x*sx + k*sk]
+// (half-chain reduced density matrix, Sec. IV bond entropy).  Tiled on CUDA
+// cores: 64x64 output tile per CTA, 16-deep K slices staged in shared memory,
+// 4x4 complex outputs per thread.
+// ---------------------------------------------------------------------------
+constexpr int kGT = 64, kGK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_kernel(const typename ZV<T>::c *psi, int n, long long K, long long sx,
+                                                   long long sk, typename ZV<T>::c *rho) {
+    typedef typename ZV<T>::c C;
+    __shared__ C As[kGK][kGT + 1];
+    __shared__ C Bs[kGK][kGT + 1];
+    const int x0 = blockIdx.y * kGT, y0 = blockIdx.x * kGT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T accr[4][4], acci[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = (T)0;
+    for (long long k0 = 0; k0 < K; k0 += kGK) {
+        // load 64 x 16 slices of rows x0.. and y0..
+        for (int idx = threadIdx.x; idx < kGT * kGK; idx += 256) {
+            int r, kk;
+            if (sk == 1) {  // contiguous along k: vary k fastest
+                r = idx / kGK;
+                kk = idx % kGK;
+            } else {        // contiguous along rows
+                kk = idx / kGT;
+                r = idx % kGT;
+            }
+            const long long k = k0 + kk;
+            C a = C{(T)0, (T)0}, b = C{(T)0, (T)0};
+            if (k < K) {
+                if (x0 + r < n) a = psi[(long long)(x0 + r) * sx + k * sk];
+                if (y0 + r < n) b = psi[(long long)(y0 + r) * sx + k * sk];
+            }
+            As[kk][r] = a;
+            Bs[kk][r] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; ++kk) {
+            C a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // a * conj(b)
+                    accr[i][j] = fma(a[i].x, b[j].x, fma(a[i].y, b[j].y, accr[i][j]));
+                    acci[i][j] = fma(a[i].y, b[j].x, fma(-a[i].x, b[j].y, acci[i][j]));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = x0 + ty + 16 * i, y = y0 + tx + 16 * j;
+            if (x < n && y < n) rho[(size_t)x * n + y] = C{accr[i][j], acci[i][j]};
+        }
+}
+
+cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_out) {
+    const int L = h->L;
+    const int l = cut;
+    int n;
+    long long K, sx, sk;
+    if (l <= L - l) {
+        n = 1 << l;
+        K = 1ll << (L - l);
+        sx = K;
+        sk = 1;
+    } else {
+        n = 1 << (L - l);
+        K = 1ll << l;
+        sx = 1;
+        sk = n;
+    }
+    *n_out = n;
+    dim3 grid((n + kGT - 1) / kGT, (n + kGT - 1) / kGT);
+    if (h->prec == OSMPS_FP64)
+        gram_kernel<double><<<grid, 256, 0, h->stream>>>((const double2 *)psi, n, K, sx, sk, (double2 *)rho);
+    else
+        gram_kernel<float><<<grid, 256, 0, h->stream>>>((const float2 *)psi, n, K, sx, sk, (float2 *)rho);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Spectrum of rho by cuSOLVER heevd (loaded at first use) and the entropy
+// ---------------------------------------------------------------------------
+struct SolverLib {
+    bool tried = false;
+    bool ok = false;
+    void *so = nullptr;
+    cusolverDnHandle_t handle = nullptr;
+    decltype(&cusolverDnCreate) create = nullptr;
+    decltype(&cusolverDnSetStream) set_stream = nullptr;
+    decltype(&cusolverDnZheevd_bufferSize) z_bufsize = nullptr;
+    decltype(&cusolverDnZheevd) z_eig = nullptr;
+    decltype(&cusolverDnCheevd_bufferSize) c_bufsize = nullptr;
+    decltype(&cusolverDnCheevd) c_eig = nullptr;
+};
+static SolverLib g_solver;
+
+static bool load_solver() {
+    if (g_solver.tried) return g_solver.ok;
+    g_solver.tried = true;
+    const char *names[] = {"libcusolver.so.12", "libcusolver.so", "libcusolver.so.11"};
+    for (const char *nm : names) {
+        g_solver.so = dlopen(nm, RTLD_NOW | RTLD_LOCAL);
+        if (g_solver.so) break;
+    }
+    if (!g_solver.so) return false;
+    g_solver.create = (decltype(g_solver.create))dlsym(g_solver.so, "cusolverDnCreate");
+    g_solver.set_stream = (decltype(g_solver.set_stream))dlsym(g_solver.so, "cusolverDnSetStream");
+    g_solver.z_bufsize = (decltype(g_solver.z_bufsize))dlsym(g_solver.so, "cusolverDnZheevd_bufferSize");
+    g_solver.z_eig = (decltype(g_solver.z_eig))dlsym(g_solver.so, "cusolverDnZheevd");
+    g_solver.c_bufsize = (decltype(g_solver.c_bufsize))dlsym(g_solver.so, "cusolverDnCheevd_bufferSize");
+    g_solver.c_eig = (decltype(g_solver.c_eig))dlsym(g_solver.so, "cusolverDnCheevd");
+    if (!g_solver.create || !g_solver.set_stream || !g_solver.z_bufsize || !g_solver.z_eig || !g_solver.c_bufsize ||
+        !g_solver.c_eig)
+        return false;
+    if (g_solver.create(&g_solver.handle) != CUSOLVER_STATUS_SUCCESS) return false;
+    g_solver.ok = true;
+    return true;
+}
+
+// S = -sum lambda ln lambda over lambda > 0; lambda (ascending, T) -> descending FP64
+template <typename T>
+__global__ void entropy_kernel(const T *w, int n, double *lambda, double *S) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double l = (double)w[i];
+        lambda[n - 1 - i] = l;
+        if (l > 0.0) s -= l * log(l);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        *S = t;
+    }
+}
+
+osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev) {
+    if (!load_solver()) return OSMPS_EUNSUPPORTED;
+    if (g_solver.set_stream(g_solver.handle, h->stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+    int lwork = 0;
+    const bool dbl = (h->prec == OSMPS_FP64);
+    cusolverStatus_t st;
+    const size_t wbytes = (dbl ? sizeof(double) : sizeof(float)) * (size_t)n;
+    if (dbl)
+        st = g_solver.z_bufsize(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                (const cuDoubleComplex *)rho, n, (const double *)nullptr, &lwork);
+    else
+        st = g_solver.c_bufsize(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                (const cuComplex *)rho, n, (const float *)nullptr, &lwork);
+    if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+    const size_t need = (size_t)lwork * (dbl ? sizeof(cuDoubleComplex) : sizeof(cuComplex)) + wbytes + 64;
+    if (need > h->solver_ws_bytes) {
+        if (h->solver_ws) dev_free(h, h->solver_ws, h->solver_ws_bytes);
+        h->solver_ws = nullptr;
+        h->solver_ws_bytes = 0;
+        cudaError_t err;
+        h->solver_ws = dev_alloc(h, need, &err);
+        if (err != cudaSuccess) return OSMPS_ENOMEM;
+        h->solver_ws_bytes = need;
+    }
+    char *ws = (char *)h->solver_ws;
+    int *info = (int *)ws;
+    void *wvals = ws + 16;
+    void *work = ws + 16 + ((wbytes + 15) & ~(size_t)15);
+    if (dbl)
+        st = g_solver.z_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                            (cuDoubleComplex *)rho, n, (double *)wvals, (cuDoubleComplex *)work, lwork, info);
+    else
+        st = g_solver.c_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n, (cuComplex *)rho,
+                            n, (float *)wvals, (cuComplex *)work, lwork, info);
+    if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+    if (dbl)
+        entropy_kernel<double><<<1, 1024, 0, h->stream>>>((const double *)wvals, n, lambda_dev, S_dev);
+    else
+        entropy_kernel<float><<<1, 1024, 0, h->stream>>>((const float *)wvals, n, lambda_dev, S_dev);
+    h->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
+}
+
+}  // namespace osmps

@@ -1,0 +1,110 @@
+"""H.psi through the C ABI against the FP64 oracle (element by element)."""
+import numpy as np
+import pytest
+import torch
+
+import seeded_inputs as si
+from oracle import ed_oracle as O
+from _gpu import TOL, Gathered, rel, seeded_device_state, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "mixed"]
+
+
+def chain_for(L, Jr, hk, prec):
+    from paper_1802_10052_gb300 import Chain
+    c = Chain(L, couplings=list(Jr), prec=prec)
+    c.set_site_fields(list(hk))
+    return c
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 7, 8, 11, 12, 13, 14, 15, 16, 17, 18, 20])
+def test_apply_H_matches_csr(L, prec):
+    rng = np.random.default_rng(100 + L)
+    Jr = rng.normal(size=L - 1)
+    hk = rng.normal(size=L)
+    c = chain_for(L, Jr, hk, prec)
+    psi = si.gaussian_state(L, L)
+    x = to_dev(psi, prec)
+    ref = O.hamiltonian_csr(L, Jr, hk) @ x.cpu().numpy().astype(np.complex128)
+    out = c.new_state()
+    c.apply_H(x, out)
+    got = to_host(out)
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    scale = np.max(np.abs(ref))
+    np.testing.assert_allclose(got, ref, rtol=0, atol=tol * scale * 10)
+    assert rel(got, ref) < tol
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_apply_H_models_and_signs(prec):
+    # nearest neighbour (alpha=None) and power law, both signs, uniform field
+    from paper_1802_10052_gb300 import Chain
+    L = 15
+    psi = si.gaussian_state(L, 3)
+    for J, alpha, h in [(-1.0, None, -1.0), (1.0, 1.5, 0.8), (-0.7, 0.0, 2.0), (1.0, 3.0, -0.3)]:
+        c = Chain(L, J=J, alpha=alpha, h=h, prec=prec)
+        Jr = O.coupling_table(L, J, alpha)
+        x = to_dev(psi, prec)
+        ref = O.RuleSetH(L, Jr, h)(x.cpu().numpy().astype(np.complex128))
+        out = c.new_state()
+        c.apply_H(x, out)
+        assert rel(to_host(out), ref) < (1e-13 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_apply_H_product_states_and_set_field(prec):
+    from paper_1802_10052_gb300 import Chain
+    L = 16
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+    x = c.new_state()
+    Jr = O.coupling_table(L, 1.0, 1.5)
+    for b in (0, si.neel_index(L), (1 << L) - 1, 12345):
+        c.init_basis_state(x, b)
+        out = c.new_state()
+        c.apply_H(x, out)
+        got = to_host(out)
+        ref = O.apply_H_rows(L, Jr, 0.8, si.basis_state(L, b), np.arange(1 << L))
+        assert rel(got, ref) < (1e-14 if prec == "fp64" else 1e-7)
+    c.set_field(0.0)
+    c.init_basis_state(x, 777)
+    c.apply_H(x, out)
+    got = to_host(out)
+    E = O.diagonal_energy(L, Jr, np.array([777]))[0]
+    assert abs(got[777] - E) < 1e-12 * abs(E) + (1e-5 if prec == "mixed" else 0)
+    assert np.count_nonzero(got) == 1
+
+
+def test_energy_call():
+    from paper_1802_10052_gb300 import Chain
+    L = 14
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="fp64")
+    psi = si.gaussian_state(L, 5) * 1.7
+    x = to_dev(psi, "fp64")
+    e, n2 = c.energy(x)
+    ref = O.RuleSetH(L, O.coupling_table(L, 1.0, 1.5), 0.8)
+    assert abs(e - np.vdot(psi, ref(psi)).real) < 1e-12 * abs(e)
+    assert abs(n2 - np.vdot(psi, psi).real) < 1e-13
+
+
+@pytest.mark.parametrize("L,prec", [(24, "fp64"), (24, "mixed"), (28, "mixed"), (28, "fp64"), (30, "mixed")])
+def test_apply_H_full_size_sampled_rows(L, prec):
+    """At the workload sizes: rows sampled across the whole index range, each
+    checked against the oracle's row-definition product."""
+    from paper_1802_10052_gb300 import Chain
+    alpha, h = (1.5, 0.8) if L != 30 else (1.0, 1.2)
+    c = Chain(L, J=1.0, alpha=alpha, h=h, prec=prec)
+    x = seeded_device_state(L, 28, prec)
+    out = c.new_state()
+    c.apply_H(x, out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(L)
+    rows = np.concatenate([rng.integers(0, 1 << L, size=3000), [0, 1, (1 << L) - 1, (1 << (L - 1)), 8191, 8192]])
+    Jr = O.coupling_table(L, 1.0, alpha)
+    ref = O.apply_H_rows(L, Jr, h, Gathered(x), rows)
+    got = Gathered(out)[rows]
+    assert rel(got, ref) < (1e-13 if prec == "fp64" else 1e-6)
+    del out, x, c
+    torch.cuda.empty_cache()

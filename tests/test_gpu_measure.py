@@ -1,0 +1,75 @@
+"""Measurements through the C ABI against the oracle's reduced density matrices."""
+import math
+
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+from oracle import ed_oracle as O
+from _gpu import rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def Chain(*a, **k):
+    from paper_1802_10052_gb300 import Chain as _C
+    return _C(*a, **k)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 9, 10, 11, 14, 16])
+def test_local_and_corr_match_rdm_route(L, prec):
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
+    psi = si.gaussian_state(L, 40 + L) * 0.9
+    x = to_dev(psi, prec)
+    ref_state = x.cpu().numpy().astype(np.complex128)
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(c.measure_local(x), O.measure_local(ref_state, L), atol=tol)
+    np.testing.assert_allclose(c.measure_corr(x), O.measure_corr(ref_state, L), atol=tol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_special_states(prec):
+    L = 12
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
+    x = c.new_state()
+    c.init_basis_state(x, si.neel_index(L))
+    np.testing.assert_allclose(c.measure_local(x), [(-1) ** k for k in range(L)], atol=0)
+    np.testing.assert_allclose(c.measure_corr(x), [[(-1) ** (i + j) for j in range(L)] for i in range(L)], atol=0)
+    assert abs(c.schmidt_entropy(x)) < 1e-6
+    g = to_dev(si.ghz_state(L), prec)
+    np.testing.assert_allclose(c.measure_local(g), 0.0, atol=1e-7)
+    np.testing.assert_allclose(c.measure_corr(g), 1.0, atol=1e-6)
+    S, lam = c.schmidt_entropy(g, spectrum=True)
+    assert abs(S - math.log(2.0)) < (1e-13 if prec == "fp64" else 1e-6)
+    np.testing.assert_allclose(lam[:2], 0.5, atol=1e-7)
+    np.testing.assert_allclose(lam[2:], 0.0, atol=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("L,cut", [(2, 1), (3, -1), (3, 2), (8, -1), (9, -1), (9, 2), (9, 7), (12, -1), (13, -1), (13, 9)])
+def test_schmidt_spectrum_matches_oracle(L, cut, prec):
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
+    psi = si.gaussian_state(L, 60 + L)
+    x = to_dev(psi, prec)
+    ref_state = x.cpu().numpy().astype(np.complex128)
+    l = L // 2 if cut == -1 else cut
+    want = O.schmidt_spectrum(ref_state, L, l)
+    S, lam = c.schmidt_entropy(x, cut=cut, spectrum=True)
+    n = 1 << min(l, L - l)
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(lam, want[:n], atol=tol)
+    assert abs(S - O.entropy_from_spectrum(want)) < (1e-12 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_page_value_L20(prec):
+    L = 20
+    m = n = 1 << (L // 2)
+    page = sum(1.0 / k for k in range(n + 1, m * n + 1)) - (m - 1) / (2.0 * n)
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
+    x = to_dev(si.gaussian_state(L, 7), prec)
+    S, lam = c.schmidt_entropy(x, spectrum=True)
+    assert abs(S - page) < 2e-3
+    assert abs(lam.sum() - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
+    assert lam.min() > -1e-6
