@@ -143,9 +143,10 @@ def test_conservation_laws(prec):
     e1, n1 = c.energy(x)
     p1 = torch.vdot(x, x[flip]).item()
     tol = 1e-10 if prec == "fp64" else 1e-5
-    assert abs(n1 - n0) < tol
-    assert abs(e1 - e0) < tol * abs(e0)
-    assert abs(p1 - p0) < tol
+    # scalars: |a - b| <= tol * max(|b|, 1)
+    assert abs(n1 - n0) < tol * max(abs(n0), 1.0)
+    assert abs(e1 - e0) < tol * max(abs(e0), 1.0)
+    assert abs(p1 - p0) < tol * max(abs(p0), 1.0)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
