@@ -148,8 +148,7 @@ def run_ours(args, rank, world):
 
     def step(x):
         chain.krylov_evolve(x, dt, nk, m)
-        sz = chain.measure_local(x)
-        zz = chain.measure_corr(x)
+        sz, zz = chain.measure_zz(x)
         S = chain.schmidt_entropy(x)
         return sz, zz, S
 

@@ -176,6 +176,9 @@ osmps_status osmps_ed_measure_local(osmps_ed_t *ed, const void *psi, double *sz)
  */
 osmps_status osmps_ed_measure_corr(osmps_ed_t *ed, const void *psi, double *szsz);
 
+/* Both of the above from one pass over the state (either output may be NULL). */
+osmps_status osmps_ed_measure_zz(osmps_ed_t *ed, const void *psi, double *sz, double *szsz);
+
 /*
  * Schmidt spectrum and entanglement entropy of the bipartition sites 1..cut |
  * cut+1..L (Sec. IV, bond entropy: rho = M M^dagger with M the state reshaped

@@ -180,6 +180,15 @@ class Chain:
               "osmps_ed_measure_corr")
         return out
 
+    def measure_zz(self, psi):
+        """(<sz_k> for k = 1..L, <sz_i sz_j> as L x L) from one pass."""
+        self._check_state(psi)
+        sz = np.zeros(self.L)
+        zz = np.zeros((self.L, self.L))
+        check(lib.osmps_ed_measure_zz(self._h, _dptr(psi), sz.ctypes.data_as(C.POINTER(C.c_double)),
+                                      zz.ctypes.data_as(C.POINTER(C.c_double))), "osmps_ed_measure_zz")
+        return sz, zz
+
     def schmidt_entropy(self, psi, cut=-1, spectrum=False):
         """Returns S, or (S, lambda descending) with spectrum=True."""
         self._check_state(psi)

@@ -360,7 +360,7 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
         hd->partials_cap = g * 4;
         hd->partials = (double *)dev_alloc(hd, sizeof(double) * hd->partials_cap, &err);
         if (err != cudaSuccess) break;
-        const size_t zneed = g * ((size_t)(L * L + L + 1) + 1024);
+        const size_t zneed = (g + 1) * ((size_t)(L * L + L + 1) + 4096);
         const size_t dneed = g * 2 * (kMaxLanczos + 1);
         hd->partials2_cap = zneed > dneed ? zneed : dneed;
         hd->partials2 = (double *)dev_alloc(hd, sizeof(double) * hd->partials2_cap, &err);
@@ -608,6 +608,19 @@ osmps_status osmps_ed_measure_corr(osmps_ed_t *ed, const void *psi, double *szsz
     CKS(check_state_ptr(h, psi));
     CK(launch_zstats(h, psi, h->dscratch));
     CK(cudaMemcpyAsync(szsz, h->dscratch + h->L, sizeof(double) * h->L * h->L, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_measure_zz(osmps_ed_t *ed, const void *psi, double *sz, double *szsz) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    CK(launch_zstats(h, psi, h->dscratch));
+    if (sz) CK(cudaMemcpyAsync(sz, h->dscratch, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
+    if (szsz)
+        CK(cudaMemcpyAsync(szsz, h->dscratch + h->L, sizeof(double) * h->L * h->L, cudaMemcpyDeviceToHost,
+                           h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return OSMPS_OK;
 }

@@ -35,25 +35,31 @@ template <typename T> struct Cx;
 template <> struct Cx<float> {
     typedef float2 c;
     typedef float4 v16;
-    static constexpr int VE = 2;   // amplitudes per 16-byte vector
+    static constexpr int VE = 2;     // amplitudes per 16-byte vector
     static constexpr int LOGVE = 1;
+    static constexpr int BLOG = 4;   // log2 amplitudes per register block (8 vectors)
 };
 template <> struct Cx<double> {
     typedef double2 c;
     typedef double2 v16;
     static constexpr int VE = 1;
     static constexpr int LOGVE = 0;
+    static constexpr int BLOG = 3;
 };
+
+constexpr int kBV = 8;                                  // 16-byte vectors per register block
+constexpr int kTileV = 1 << (kTileBytesLog2 - 4);       // 16-byte vectors per tile
+constexpr int kTab = 256;                               // TA (<= 64) + TB (<= 128) per stage
+static_assert(kTileV == kBV * kPassThreads, "one register block per thread per tile");
 
 template <typename T>
 struct PassParams {
-    const typename Cx<T>::v16 *u;
-    const typename Cx<T>::v16 *acc;
+    const typename Cx<T>::v16 *u;       // vector being multiplied (tile staged in shared memory)
+    const typename Cx<T>::v16 *stream;  // elementwise input: previous Lanczos vector (first pass) or partial sum
     typename Cx<T>::v16 *out;
-    const typename Cx<T>::v16 *uprev;
     const T *Ell;
     const T *Fhh;
-    const double *epi;
+    const double *epi;                  // sv, a, b (device) or null
     double *partials;
     const int *m_eff;
     long long ntiles;
@@ -62,7 +68,6 @@ struct PassParams {
     T hb[kMaxL + 1];
 };
 
-// 16-byte vector <-> amplitudes
 __device__ __forceinline__ void unpack(const float4 &v, float2 *e) {
     e[0] = make_float2(v.x, v.y);
     e[1] = make_float2(v.z, v.w);
@@ -71,10 +76,20 @@ __device__ __forceinline__ float4 pack(const float2 *e) { return make_float4(e[0
 __device__ __forceinline__ void unpack(const double2 &v, double2 *e) { e[0] = v; }
 __device__ __forceinline__ double2 pack(const double2 *e) { return e[0]; }
 
-template <typename V>
-__device__ __forceinline__ V ld_stream(const V *p) {
-    return __ldcs(p);
+// acc += f * x on a complex amplitude: one packed FP32x2 FMA, or two FP64 FMAs
+__device__ __forceinline__ void cfma(float f, const float2 &x, float2 &acc) {
+    unsigned long long X = ((unsigned long long)__float_as_uint(x.y) << 32) | __float_as_uint(x.x);
+    unsigned long long F = ((unsigned long long)__float_as_uint(f) << 32) | __float_as_uint(f);
+    unsigned long long A = ((unsigned long long)__float_as_uint(acc.y) << 32) | __float_as_uint(acc.x);
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(A) : "l"(F), "l"(X));
+    acc.x = __uint_as_float((unsigned)A);
+    acc.y = __uint_as_float((unsigned)(A >> 32));
 }
+__device__ __forceinline__ void cfma(double f, const double2 &x, double2 &acc) {
+    acc.x = fma(f, x.x, acc.x);
+    acc.y = fma(f, x.y, acc.y);
+}
+
 template <typename V>
 __device__ __forceinline__ void st_stream(V *p, const V &v) {
     __stcs(p, v);
@@ -115,27 +130,46 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
+// swizzled position of vector v of register block blk: the 8 vectors of a
+// block are rotated so that the 8 lanes of a quarter warp reading "vector v of
+// their own block" hit 8 different 16-byte bank groups
+__device__ __forceinline__ int swz(int blk, int v) { return (blk << 3) | (v ^ (blk & 7)); }
+
+// One pass of the product.  Persistent: one 512-thread CTA per SM walks the
+// tiles; the tile of u for the next iteration is copied asynchronously into
+// the second shared-memory stage while the current one is computed, and the
+// elementwise stream (previous vector or partial sum) of each thread's own
+// register block is copied asynchronously one tile ahead.
 template <typename T>
-__global__ void __launch_bounds__(kPassThreads, 2) hpsi_pass_kernel(PassParams<T> p) {
+__global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T> p) {
     typedef typename Cx<T>::c C;
     typedef typename Cx<T>::v16 V;
     constexpr int VE = Cx<T>::VE;
     constexpr int LOGVE = Cx<T>::LOGVE;
+    constexpr int BLOG = Cx<T>::BLOG;
+    constexpr int BE = kBV * VE;  // amplitudes per register block
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *tile = reinterpret_cast<V *>(smem_raw);
-    T *TA = reinterpret_cast<T *>(smem_raw + (1u << kTileBytesLog2));
-    T *TB = TA + 128;
+    V *U0 = reinterpret_cast<V *>(smem_raw);
+    V *U1 = U0 + kTileV;
+    V *S = U1 + kTileV;
+    T *tab0 = reinterpret_cast<T *>(S + kTileV);
+    T *tab1 = tab0 + kTab;
 
     if (p.m_eff != nullptr && *p.m_eff <= p.stop_index) return;
 
+    const int tid = threadIdx.x;
     const int tbits = p.c + p.g;
     const int nvec = (1 << tbits) >> LOGVE;
     const uint64_t cmask = (1ull << p.c) - 1ull;
     const int oc = p.o - p.c;
     const uint64_t ocmask = (1ull << oc) - 1ull;
+    const bool has_stream = p.stream != nullptr;
 
     double sv = 1.0, ea = 0.0, eb = 0.0;
     if (p.epi != nullptr) {
@@ -143,125 +177,168 @@ __global__ void __launch_bounds__(kPassThreads, 2) hpsi_pass_kernel(PassParams<T
         ea = p.epi[1];
         eb = p.epi[2];
     }
-    const T svT = (T)sv, eaT = (T)(ea * sv), ebT = (T)eb;
-    double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
+    // first pass: r = H_inner u - a u - (b/sv) uprev ;  last pass: w = sv * r
+    const T aT = (T)ea;
+    const T bsT = (p.first && has_stream) ? (T)(-eb / sv) : (T)1;
+    const T svT = (T)sv;
 
-    for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+    auto tile_base = [&](long long t) -> uint64_t {
         const uint64_t tt = (uint64_t)t;
-        const uint64_t base = ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
+        return ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
+    };
+    auto gidx = [&](uint64_t base, int q) -> uint64_t {  // global 16-byte vector index of tile vector q
+        const int li = q << LOGVE;
+        return (base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask)) >> LOGVE;
+    };
+    auto issue_u = [&](long long t, V *buf) {
+        const uint64_t base = tile_base(t);
+#pragma unroll
+        for (int i = 0; i < kBV; ++i) {
+            const int q = i * kPassThreads + tid;
+            if (q < nvec) cp_async16(&buf[swz(q >> 3, q & 7)], &p.u[gidx(base, q)]);
+        }
+    };
+    auto issue_s = [&](long long t) {
+        const uint64_t base = tile_base(t);
+#pragma unroll
+        for (int v = 0; v < kBV; ++v) {
+            const int q = tid * kBV + v;
+            if (q < nvec) cp_async16(&S[q], &p.stream[gidx(base, q)]);
+        }
+    };
+    auto build_tab = [&](long long t, T *tab) {
+        const int a = p.g, ta = p.ta, tb = a - ta;
+        const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
+        if (tid < (1 << ta)) {
+            T s = F[a];
+            for (int j = 0; j < ta; ++j) s += ((tid >> j) & 1) ? -F[j] : F[j];
+            tab[tid] = s;
+        } else if (tid < (1 << ta) + (1 << tb)) {
+            const int y = tid - (1 << ta);
+            T s = (T)0;
+            for (int j = 0; j < tb; ++j) s += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
+            tab[64 + y] = s;
+        }
+    };
 
-        // ---- stage the tile: asynchronous 16-byte copies global -> shared ----
-        for (int q = threadIdx.x; q < nvec; q += kPassThreads) {
-            const int li = q << LOGVE;
-            const uint64_t b = base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask);
-            cp_async16(&tile[q], &p.u[b >> LOGVE]);
+    double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
+    long long t = blockIdx.x;
+    if (t < p.ntiles) {
+        issue_u(t, U0);
+        cp_async_commit();
+        if (has_stream) issue_s(t);
+        cp_async_commit();
+        if (p.first) build_tab(t, tab0);
+    }
+    int stage = 0;
+    const int blk = tid;
+    const bool active = (blk * kBV) < nvec;
+    for (; t < p.ntiles; t += gridDim.x, stage ^= 1) {
+        const long long tn = t + gridDim.x;
+        V *Ucur = stage ? U1 : U0;
+        V *Unext = stage ? U0 : U1;
+        T *tcur = stage ? tab1 : tab0;
+        T *tnext = stage ? tab0 : tab1;
+        cp_async_wait<1>();
+        __syncthreads();
+        if (tn < p.ntiles) {
+            issue_u(tn, Unext);
+            if (p.first) build_tab(tn, tnext);
         }
         cp_async_commit();
-        if (p.first) {
-            // per-tile diagonal tables (overlap with the copies in flight)
-            const int a = p.g, ta = p.ta, tb = a - ta;
-            const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
-            const int x = threadIdx.x;
-            if (x < (1 << ta)) {
-                T s = F[a];
-                for (int j = 0; j < ta; ++j) s += ((x >> j) & 1) ? -F[j] : F[j];
-                TA[x] = s;
-            } else if (x < (1 << ta) + (1 << tb)) {
-                const int y = x - (1 << ta);
-                T s = (T)0;
-                for (int j = 0; j < tb; ++j) s += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
-                TB[y] = s;
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();
 
-        // ---- compute ----
+        const uint64_t base = tile_base(t);
         T pd0 = 0, pd1 = 0, pn = 0;
-        for (int q = threadIdx.x; q < nvec; q += kPassThreads) {
-            const int li0 = q << LOGVE;
-            const uint64_t b0 = base | ((uint64_t)(li0 >> p.c) << p.o) | ((uint64_t)li0 & cmask);
-            C self[VE], r[VE];
-            unpack(tile[q], self);
+        if (active) {
+            C self[BE], r[BE];
 #pragma unroll
-            for (int e = 0; e < VE; ++e) r[e] = C{(T)0, (T)0};
-
-            int k0 = 0;
-            if (VE == 2 && p.c == 0) {
-                // bit 0 lives inside the 16-byte vector
-                const T f = p.hb[p.o];
-                r[0].x = fma(f, self[VE - 1].x, r[0].x);
-                r[0].y = fma(f, self[VE - 1].y, r[0].y);
-                r[VE - 1].x = fma(f, self[0].x, r[VE - 1].x);
-                r[VE - 1].y = fma(f, self[0].y, r[VE - 1].y);
-                k0 = 1;
-            }
-            for (int k = k0; k < p.g; ++k) {
-                const T f = p.hb[p.o + k];
-                C nb[VE];
-                unpack(tile[q ^ (1 << (p.c + k - LOGVE))], nb);
+            for (int v = 0; v < kBV; ++v) unpack(Ucur[swz(blk, v)], &self[v * VE]);
 #pragma unroll
-                for (int e = 0; e < VE; ++e) {
-                    r[e].x = fma(f, nb[e].x, r[e].x);
-                    r[e].y = fma(f, nb[e].y, r[e].y);
+            for (int e = 0; e < BE; ++e) r[e] = C{(T)0, (T)0};
+            // flips of bits inside the register block
+#pragma unroll
+            for (int lb = 0; lb < BLOG; ++lb) {
+                if (lb >= p.c && lb < tbits) {
+                    const T f = p.hb[p.o + lb - p.c];
+#pragma unroll
+                    for (int e = 0; e < BE; ++e) cfma(f, self[e ^ (1 << lb)], r[e]);
                 }
             }
-
+            // flips of bits across register blocks (neighbour block in shared memory)
+            const int k0 = (p.c > BLOG ? p.c : BLOG);
+            for (int lb = k0; lb < tbits; ++lb) {
+                const T f = p.hb[p.o + lb - p.c];
+                const int nb = blk ^ (1 << (lb - BLOG));
+#pragma unroll
+                for (int v = 0; v < kBV; ++v) {
+                    C x[VE];
+                    unpack(Ucur[swz(nb, v)], x);
+#pragma unroll
+                    for (int e = 0; e < VE; ++e) cfma(f, x[e], r[v * VE + e]);
+                }
+            }
             if (p.first) {
+                // diagonal: E(b) - a on the 16 (8) amplitudes of this block
+                const int li0 = blk * BE;
                 const int tmask = (1 << p.ta) - 1;
 #pragma unroll
-                for (int e = 0; e < VE; ++e) {
+                for (int e = 0; e < BE; ++e) {
                     const int li = li0 + e;
-                    const T E = __ldg(&p.Ell[li]) + TA[li & tmask] + TB[li >> p.ta];
-                    r[e].x = fma(E, self[e].x, r[e].x);
-                    r[e].y = fma(E, self[e].y, r[e].y);
-                }
-            } else {
-                C a[VE];
-                unpack(ld_stream(&p.acc[b0 >> LOGVE]), a);
-#pragma unroll
-                for (int e = 0; e < VE; ++e) {
-                    r[e].x += a[e].x;
-                    r[e].y += a[e].y;
+                    const T E = __ldg(&p.Ell[li]) + tcur[li & tmask] + tcur[64 + (li >> p.ta)] - aT;
+                    cfma(E, self[e], r[e]);
                 }
             }
-
+            if (has_stream) {
+                cp_async_wait<1>();  // this thread's stream copies of tile t have landed
+#pragma unroll
+                for (int v = 0; v < kBV; ++v) {
+                    C x[VE];
+                    unpack(S[blk * kBV + v], x);
+#pragma unroll
+                    for (int e = 0; e < VE; ++e) cfma(bsT, x[e], r[v * VE + e]);
+                }
+            }
             if (!p.last) {
-                p.out[b0 >> LOGVE] = pack(r);
-            } else if (p.epilogue == EPI_PLAIN) {
-                st_stream(&p.out[b0 >> LOGVE], pack(r));
-            } else if (p.epilogue == EPI_KRYLOV) {
-                C up[VE];
-                if (p.uprev != nullptr) {
-                    unpack(ld_stream(&p.uprev[b0 >> LOGVE]), up);
-                } else {
 #pragma unroll
-                    for (int e = 0; e < VE; ++e) up[e] = C{(T)0, (T)0};
+                for (int v = 0; v < kBV; ++v)
+                    if (blk * kBV + v < nvec) p.out[gidx(base, blk * kBV + v)] = pack(&r[v * VE]);
+            } else if (p.epilogue == EPI_ENERGY) {
+#pragma unroll
+                for (int e = 0; e < BE; ++e) {
+                    if (((blk * BE + e) >> LOGVE) < nvec) {
+                        pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
+                        pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
+                        pn = fma(self[e].x, self[e].x, fma(self[e].y, self[e].y, pn));
+                    }
                 }
-                C w[VE];
+            } else {
 #pragma unroll
-                for (int e = 0; e < VE; ++e) {
-                    w[e].x = svT * r[e].x - eaT * self[e].x - ebT * up[e].x;
-                    w[e].y = svT * r[e].y - eaT * self[e].y - ebT * up[e].y;
-                    pd0 = fma(self[e].x, w[e].x, fma(self[e].y, w[e].y, pd0));
-                    pd1 = fma(self[e].x, w[e].y, fma(-self[e].y, w[e].x, pd1));
-                    pn = fma(w[e].x, w[e].x, fma(w[e].y, w[e].y, pn));
+                for (int e = 0; e < BE; ++e) {
+                    r[e].x *= svT;
+                    r[e].y *= svT;
                 }
-                st_stream(&p.out[b0 >> LOGVE], pack(w));
-            } else {  // EPI_ENERGY
 #pragma unroll
-                for (int e = 0; e < VE; ++e) {
-                    pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
-                    pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
-                    pn = fma(self[e].x, self[e].x, fma(self[e].y, self[e].y, pn));
+                for (int v = 0; v < kBV; ++v)
+                    if (blk * kBV + v < nvec) st_stream(&p.out[gidx(base, blk * kBV + v)], pack(&r[v * VE]));
+                if (p.epilogue == EPI_KRYLOV) {
+#pragma unroll
+                    for (int e = 0; e < BE; ++e) {
+                        if (((blk * BE + e) >> LOGVE) < nvec) {
+                            pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
+                            pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
+                            pn = fma(r[e].x, r[e].x, fma(r[e].y, r[e].y, pn));
+                        }
+                    }
                 }
             }
         }
         acc_d0 += (double)pd0;
         acc_d1 += (double)pd1;
         acc_n += (double)pn;
-        __syncthreads();
+        if (has_stream && tn < p.ntiles && active) issue_s(tn);
+        cp_async_commit();
     }
+    cp_async_wait<0>();
 
     if (p.last && p.epilogue != EPI_PLAIN && p.partials != nullptr) {
         block_reduce3<T>(acc_d0 * sv, acc_d1 * sv, acc_n, p.partials + 4 * (size_t)blockIdx.x);
@@ -342,7 +419,7 @@ PassPlan make_plan(int L, int prec) {
     return pl;
 }
 
-static size_t pass_smem() { return (1u << kTileBytesLog2) + 256 * sizeof(double); }
+static size_t pass_smem() { return 3u * (1u << kTileBytesLog2) + 2 * kTab * sizeof(double); }
 
 template <typename T>
 static int grid_for(Handle *h, long long ntiles) {
@@ -414,9 +491,8 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         }
         if (last && a.epilogue == EPI_ENERGY) dst = nullptr;
         p.u = reinterpret_cast<const V *>(a.u);
-        p.acc = reinterpret_cast<const V *>(src_acc);
+        p.stream = reinterpret_cast<const V *>(i == 0 ? a.uprev : src_acc);
         p.out = reinterpret_cast<V *>(dst);
-        p.uprev = reinterpret_cast<const V *>(a.uprev);
         p.Ell = reinterpret_cast<const T *>(h->Ell);
         p.Fhh = reinterpret_cast<const T *>(h->Fhh);
         p.epi = a.epi;

@@ -19,7 +19,8 @@
 namespace osmps {
 
 constexpr int kZThreads = 256;
-constexpr int kZTileBits = 10;
+constexpr int kZTileBits = 12;                  // 4096 amplitudes per tile
+constexpr int kZPer = (1 << kZTileBits) / kZThreads;  // amplitudes per thread (16)
 
 template <typename T> struct ZV;
 template <> struct ZV<float> {
@@ -32,56 +33,67 @@ template <> struct ZV<double> {
 // number of per-CTA accumulators: C (L*L) + m (L) + total
 __host__ __device__ inline int zacc_count(int L) { return L * L + L + 1; }
 
+// One streaming pass over p_b = |psi_b|^2.  Per thread: 16 amplitudes at
+// li = tid + 256 k; sums over a thread and warp in T (FP32 in mixed mode),
+// across warps, tiles and CTAs in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) zstats_kernel(const typename ZV<T>::c *psi, int L, int t,
                                                            long long ntiles, double *blockacc, double *Gpart) {
     const int nel = 1 << t;
-    const int per = (nel + kZThreads - 1) / kZThreads;   // elements per thread (<= 4)
     const int nacc = zacc_count(L);
-    const int nown = (nacc + kZThreads - 1) / kZThreads; // accumulators per thread (<= 4 for L <= 30)
+    const int nown = (nacc + kZThreads - 1) / kZThreads;  // <= 4 for L <= 30
     double own[4] = {0, 0, 0, 0};
-    double G[4] = {0, 0, 0, 0};
+    T G[kZPer];
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) G[k] = (T)0;
     __shared__ double red[kZTileBits + 1][kZThreads / 32];
     __shared__ double stat[kZTileBits + 1];  // P, M_0..M_{t-1}
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t base = (uint64_t)tile << t;
-        double v[kZTileBits + 1];
+        T pk[kZPer];
 #pragma unroll
-        for (int j = 0; j <= kZTileBits; ++j) v[j] = 0.0;
-        double Pt = 0.0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (k < per) {
-                const int li = threadIdx.x + k * kZThreads;
-                if (li < nel) {
-                    const typename ZV<T>::c a = psi[base + li];
-                    const double p = (double)(a.x * a.x + a.y * a.y);
-                    G[k] += p;
-                    Pt += p;
-                    // bits of li above the thread index
-                    for (int j = 8; j < t; ++j) v[1 + j] += ((li >> j) & 1) ? -p : p;
-                }
+        for (int k = 0; k < kZPer; ++k) {
+            const int li = threadIdx.x + k * kZThreads;
+            T pv = (T)0;
+            if (li < nel) {
+                const typename ZV<T>::c a = __ldcs(&psi[base + li]);
+                pv = a.x * a.x + a.y * a.y;
             }
+            pk[k] = pv;
+            G[k] += pv;
         }
-        v[0] = Pt;
-        for (int j = 0; j < t && j < 8; ++j) v[1 + j] = ((threadIdx.x >> j) & 1) ? -Pt : Pt;
-        // block reduction of t+1 values
-        for (int j = 0; j <= t; ++j) {
-            double s = v[j];
+        // per-thread moments: v[0] = sum p, v[1+j] = sum s_j p
+        T v[kZTileBits + 1];
+        T Pt = (T)0;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = s;
+        for (int k = 0; k < kZPer; ++k) Pt += pk[k];
+        v[0] = Pt;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[1 + j] = ((threadIdx.x >> j) & 1) ? -Pt : Pt;
+#pragma unroll
+        for (int j = 8; j < kZTileBits; ++j) {
+            T s = (T)0;
+#pragma unroll
+            for (int k = 0; k < kZPer; ++k) s += (((k << 8) >> j) & 1) ? -pk[k] : pk[k];
+            v[1 + j] = s;
+        }
+#pragma unroll
+        for (int j = 0; j <= kZTileBits; ++j) {
+            T x = v[j];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) red[j][wid] = (double)x;
         }
         __syncthreads();
         if (threadIdx.x <= t) {
-            double s = 0.0;
-            for (int w = 0; w < kZThreads / 32; ++w) s += red[threadIdx.x][w];
-            stat[threadIdx.x] = s;
+            double sacc = 0.0;
+            for (int w = 0; w < kZThreads / 32; ++w) sacc += red[threadIdx.x][w];
+            stat[threadIdx.x] = sacc;
         }
         __syncthreads();
         const double P = stat[0];
-        // per-CTA accumulators
         for (int k = 0; k < nown; ++k) {
             const int e = threadIdx.x + k * kZThreads;
             if (e >= nacc) break;
@@ -118,47 +130,61 @@ __global__ void __launch_bounds__(kZThreads) zstats_kernel(const typename ZV<T>:
         const int e = threadIdx.x + k * kZThreads;
         if (e < nacc) blockacc[(size_t)blockIdx.x * nacc + e] = own[k];
     }
-    for (int k = 0; k < per; ++k) {
+#pragma unroll
+    for (int k = 0; k < kZPer; ++k) {
         const int li = threadIdx.x + k * kZThreads;
-        if (li < nel) Gpart[(size_t)blockIdx.x * nel + li] = G[k];
+        if (li < nel) Gpart[(size_t)blockIdx.x * nel + li] = (double)G[k];
     }
 }
 
-// Sum the per-CTA partials (fixed order) and assemble the outputs in site order:
-// out[0..L) = <sz_k>, out[L..L+L*L) = <sz_i sz_j>.
-__global__ void zstats_finalize_kernel(const double *blockacc, const double *Gpart, int nblk, int L, int t,
-                                       double *out) {
+// Sum the per-CTA partials in a fixed order, one warp per entry:
+// red[0..nacc) accumulators, red[nacc..nacc+nel) the low-bit marginal G.
+__global__ void zstats_reduce_kernel(const double *blockacc, const double *Gpart, int nblk, int nacc, int nel,
+                                     double *red) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= nacc + nel) return;
+    double s = 0.0;
+    if (w < nacc) {
+        for (int b = lane; b < nblk; b += 32) s += blockacc[(size_t)b * nacc + w];
+    } else {
+        const int li = w - nacc;
+        for (int b = lane; b < nblk; b += 32) s += Gpart[(size_t)b * nel + li];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) red[w] = s;
+}
+
+// Outputs in site order, one warp per output: out[0..L) = <sz_k>,
+// out[L..L+L*L) = <sz_i sz_j>.
+__global__ void zstats_assemble_kernel(const double *red, int L, int t, double *out) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= L + L * L) return;
     const int nacc = zacc_count(L);
     const int nel = 1 << t;
-    extern __shared__ double Gs[];
-    for (int li = threadIdx.x; li < nel; li += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += Gpart[(size_t)b * nel + li];
-        Gs[li] = s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < L + L * L; e += blockDim.x) {
-        double s = 0.0;
-        if (e < L) {
-            const int site = e + 1, bit = L - site;
-            for (int b = 0; b < nblk; ++b) s += blockacc[(size_t)b * nacc + L * L + bit];
-        } else {
-            const int q = e - L;
-            const int si = q / L + 1, sj = q % L + 1;
-            const int bi = L - si, bj = L - sj;
-            if (bi == bj) {
-                for (int b = 0; b < nblk; ++b) s += blockacc[(size_t)b * nacc + L * L + L];
-            } else if (bi < t && bj < t) {
-                for (int lo = 0; lo < nel; ++lo) {
-                    const int sg = (((lo >> bi) ^ (lo >> bj)) & 1) ? -1 : 1;
-                    s += (double)sg * Gs[lo];
-                }
-            } else {
-                for (int b = 0; b < nblk; ++b) s += blockacc[(size_t)b * nacc + bi * L + bj];
+    double s = 0.0;
+    if (w < L) {
+        const int bit = L - (w + 1);
+        s = red[L * L + bit];
+    } else {
+        const int q = w - L;
+        const int bi = L - (q / L + 1), bj = L - (q % L + 1);
+        if (bi == bj) {
+            s = red[L * L + L];
+        } else if (bi < t && bj < t) {
+            double part = 0.0;
+            for (int lo = lane; lo < nel; lo += 32) {
+                const int sg = (((lo >> bi) ^ (lo >> bj)) & 1) ? -1 : 1;
+                part += (double)sg * red[nacc + lo];
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            s = part;
+        } else {
+            s = red[bi * L + bj];
         }
-        out[e] = s;
     }
+    if (lane == 0) out[w] = s;
 }
 
 template <typename T>
@@ -168,14 +194,19 @@ static cudaError_t zstats_t(Handle *h, const void *psi, double *out_dev) {
     const long long ntiles = 1ll << (L - t);
     long long cap = (long long)h->nsm * 4;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    const size_t need = (size_t)grid * (zacc_count(L) + (1u << t));
+    const int nacc = zacc_count(L), nel = 1 << t;
+    const size_t need = (size_t)grid * (nacc + nel) + nacc + nel;
     if (need > h->partials2_cap) return cudaErrorMemoryAllocation;
     double *blockacc = h->partials2;
-    double *Gpart = h->partials2 + (size_t)grid * zacc_count(L);
+    double *Gpart = h->partials2 + (size_t)grid * nacc;
+    double *red = Gpart + (size_t)grid * nel;
     zstats_kernel<T><<<grid, kZThreads, 0, h->stream>>>(reinterpret_cast<const typename ZV<T>::c *>(psi), L, t,
                                                          ntiles, blockacc, Gpart);
-    zstats_finalize_kernel<<<1, 512, sizeof(double) << t, h->stream>>>(blockacc, Gpart, grid, L, t, out_dev);
-    h->launches += 2;
+    const int nw1 = nacc + nel;
+    zstats_reduce_kernel<<<(nw1 + 7) / 8, 256, 0, h->stream>>>(blockacc, Gpart, grid, nacc, nel, red);
+    const int nw2 = L + L * L;
+    zstats_assemble_kernel<<<(nw2 + 7) / 8, 256, 0, h->stream>>>(red, L, t, out_dev);
+    h->launches += 3;
     return cudaGetLastError();
 }
 

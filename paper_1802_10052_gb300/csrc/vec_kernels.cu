@@ -418,10 +418,18 @@ __device__ int tridiag_ql(double *d, double *e, int n, double *Z, int ldz) {
     return 0;
 }
 
-// xi = ||psi|| exp(-i dt T) e_1 in the Krylov basis; coefficients include the
-// scales of the stored vectors; Saad's a-posteriori estimate
+// xi = ||psi|| exp(-i dt T) e_1 in the Krylov basis (T real symmetric
+// tridiagonal, n <= 64), by the exponential's Taylor series on the vector with
+// scaling: exp(-i dt T) e_1 = (exp(-i dt T / s))^s e_1, s chosen so that
+// ||dt T / s||_1 <= 1/2, 20 terms per factor (remainder < 2^-21 / 21! ~ 1e-26
+// relative); Moler & Van Loan, "Nineteen dubious ways", methods 1 and 3.  One
+// warp; lane i owns entries i and i + 32.  The coefficients are scaled by the
+// stored-vector scales; Saad's a-posteriori estimate beta_n |xi_{n-1}| is kept.
 __global__ void tridiag_exp_kernel(KrylovCtl *ctl, double dt) {
-    __shared__ double d[kMaxKrylov], e[kMaxKrylov], Z[kMaxKrylov * kMaxKrylov];
+    __shared__ double a[kMaxKrylov], b[kMaxKrylov + 1];      // diag, b[i] couples i-1 and i
+    __shared__ double xr[kMaxKrylov], xi[kMaxKrylov];         // running vector
+    __shared__ double tr[kMaxKrylov], ti[kMaxKrylov];         // current Taylor term
+    __shared__ int s_steps;
     const int lane = threadIdx.x;
     const int n = ctl->m_eff;
     if (n <= 0) {
@@ -429,36 +437,69 @@ __global__ void tridiag_exp_kernel(KrylovCtl *ctl, double dt) {
         return;
     }
     for (int i = lane; i < n; i += 32) {
-        d[i] = ctl->alpha[i];
-        e[i] = (i + 1 < n) ? ctl->beta[i + 1] : 0.0;
-        for (int k = 0; k < n; ++k) Z[i * kMaxKrylov + k] = (i == k) ? 1.0 : 0.0;
+        a[i] = ctl->alpha[i];
+        b[i] = (i > 0) ? ctl->beta[i] : 0.0;
+        xr[i] = (i == 0) ? 1.0 : 0.0;
+        xi[i] = 0.0;
+    }
+    if (lane == 0) b[n] = 0.0;
+    __syncwarp();
+    if (lane == 0) {
+        double nrm1 = 0.0;
+        for (int i = 0; i < n; ++i) nrm1 = fmax(nrm1, fabs(a[i]) + fabs(b[i]) + fabs(b[i + 1]));
+        const double z = fabs(dt) * nrm1;
+        int s = (int)ceil(z / 0.5);
+        s_steps = s < 1 ? 1 : s;
     }
     __syncwarp();
-    // every lane holds d, e through shared memory; run the recurrence redundantly
-    double dl[kMaxKrylov], el[kMaxKrylov];
-    for (int i = 0; i < n; ++i) {
-        dl[i] = d[i];
-        el[i] = e[i];
-    }
-    __syncwarp();
-    tridiag_ql(dl, el, n, Z, kMaxKrylov);
-    __syncwarp();
-    // xi_i = nrm * sum_l Z[i][l] exp(-i dt lambda_l) Z[0][l]
-    for (int i = lane; i < n; i += 32) {
-        double xr = 0.0, xi = 0.0;
-        for (int l = 0; l < n; ++l) {
-            double sn, cs;
-            sincos(-dt * dl[l], &sn, &cs);
-            const double w = Z[i * kMaxKrylov + l] * Z[0 * kMaxKrylov + l];
-            xr += w * cs;
-            xi += w * sn;
+    const int s = s_steps;
+    const double c = dt / (double)s;
+    for (int rep = 0; rep < s; ++rep) {
+        for (int i = lane; i < n; i += 32) {
+            tr[i] = xr[i];
+            ti[i] = xi[i];
         }
-        xr *= ctl->nrm;
-        xi *= ctl->nrm;
-        ctl->coef_re[i] = xr * ctl->scale[i];
-        ctl->coef_im[i] = xi * ctl->scale[i];
+        __syncwarp();
+        for (int k = 1; k <= 20; ++k) {
+            // term <- (-i c T term) / k
+            double nr[2], ni[2];
+            for (int q = 0; q < 2; ++q) {
+                const int i = lane + 32 * q;
+                if (i < n) {
+                    double yr = a[i] * tr[i], yi = a[i] * ti[i];
+                    if (i > 0) {
+                        yr = fma(b[i], tr[i - 1], yr);
+                        yi = fma(b[i], ti[i - 1], yi);
+                    }
+                    if (i + 1 < n) {
+                        yr = fma(b[i + 1], tr[i + 1], yr);
+                        yi = fma(b[i + 1], ti[i + 1], yi);
+                    }
+                    const double f = c / (double)k;
+                    nr[q] = f * yi;   // -i (yr + i yi) = yi - i yr
+                    ni[q] = -f * yr;
+                }
+            }
+            __syncwarp();
+            for (int q = 0; q < 2; ++q) {
+                const int i = lane + 32 * q;
+                if (i < n) {
+                    tr[i] = nr[q];
+                    ti[i] = ni[q];
+                    xr[i] += nr[q];
+                    xi[i] += ni[q];
+                }
+            }
+            __syncwarp();
+        }
+    }
+    const double nrm = ctl->nrm;
+    for (int i = lane; i < n; i += 32) {
+        const double r = xr[i] * nrm, im = xi[i] * nrm;
+        ctl->coef_re[i] = r * ctl->scale[i];
+        ctl->coef_im[i] = im * ctl->scale[i];
         if (i == n - 1) {
-            const double err = ctl->beta[n] * sqrt(xr * xr + xi * xi);
+            const double err = ctl->beta[n] * sqrt(r * r + im * im);
             ctl->err = err;
             ctl->err_sum += err;
         }

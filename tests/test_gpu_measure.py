@@ -24,8 +24,30 @@ def test_local_and_corr_match_rdm_route(L, prec):
     x = to_dev(psi, prec)
     ref_state = x.cpu().numpy().astype(np.complex128)
     tol = 1e-13 if prec == "fp64" else 1e-6
-    np.testing.assert_allclose(c.measure_local(x), O.measure_local(ref_state, L), atol=tol)
-    np.testing.assert_allclose(c.measure_corr(x), O.measure_corr(ref_state, L), atol=tol)
+    want_sz, want_zz = O.measure_local(ref_state, L), O.measure_corr(ref_state, L)
+    np.testing.assert_allclose(c.measure_local(x), want_sz, atol=tol)
+    np.testing.assert_allclose(c.measure_corr(x), want_zz, atol=tol)
+    sz, zz = c.measure_zz(x)
+    np.testing.assert_allclose(sz, want_sz, atol=tol)
+    np.testing.assert_allclose(zz, want_zz, atol=tol)
+
+
+def test_measure_full_size_invariants():
+    # L = 28: the all-up and Neel product states give exact +-1 patterns, and a
+    # seeded random state satisfies <sz_i sz_i> = <psi|psi> with |<.>| <= norm
+    from _gpu import seeded_device_state
+    L = 28
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    x = c.new_state()
+    c.init_basis_state(x, si.neel_index(L))
+    sz, zz = c.measure_zz(x)
+    np.testing.assert_allclose(sz, [(-1) ** k for k in range(L)], atol=0)
+    np.testing.assert_allclose(zz, [[(-1) ** (i + j) for j in range(L)] for i in range(L)], atol=0)
+    y = seeded_device_state(L, 3, "mixed")
+    sz, zz = c.measure_zz(y)
+    np.testing.assert_allclose(np.diag(zz), 1.0, atol=1e-6)
+    assert np.all(np.abs(sz) < 1e-3) and np.all(np.abs(zz - np.diag(np.diag(zz))) < 1e-3)
+    np.testing.assert_allclose(zz, zz.T, atol=0)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
