@@ -50,7 +50,7 @@ template <> struct Cx<double> {
 constexpr int kBV = 8;                                  // 16-byte vectors per register block
 constexpr int kTileV = 1 << (kTileBytesLog2 - 4);       // 16-byte vectors per tile
 constexpr int kTab = 256;                               // TA (<= 64) + TB (<= 128) per stage
-static_assert(kTileV == kBV * kPassThreads, "one register block per thread per tile");
+static_assert(kTileV == kBV * kPassThreads, "eight vectors per thread per tile");
 
 template <typename T>
 struct PassParams {
@@ -135,24 +135,19 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// swizzled position of vector v of register block blk: the 8 vectors of a
-// block are rotated so that the 8 lanes of a quarter warp reading "vector v of
-// their own block" hit 8 different 16-byte bank groups
-__device__ __forceinline__ int swz(int blk, int v) { return (blk << 3) | (v ^ (blk & 7)); }
-
 // One pass of the product.  Persistent: one 512-thread CTA per SM walks the
-// tiles; the tile of u for the next iteration is copied asynchronously into
-// the second shared-memory stage while the current one is computed, and the
-// elementwise stream (previous vector or partial sum) of each thread's own
-// register block is copied asynchronously one tile ahead.
+// tiles.  Thread tid owns the 16-byte vectors q = tid + 512 i (i < 8) of every
+// tile, so all global loads and stores are lane-coalesced.  The tile of u for
+// the next iteration is copied asynchronously into the second shared-memory
+// stage while the current one is computed; the elementwise stream (previous
+// vector or partial sum) of the thread's own vectors is copied one tile ahead
+// by the thread that consumes it.
 template <typename T>
 __global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T> p) {
     typedef typename Cx<T>::c C;
     typedef typename Cx<T>::v16 V;
     constexpr int VE = Cx<T>::VE;
     constexpr int LOGVE = Cx<T>::LOGVE;
-    constexpr int BLOG = Cx<T>::BLOG;
-    constexpr int BE = kBV * VE;  // amplitudes per register block
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *U0 = reinterpret_cast<V *>(smem_raw);
@@ -195,14 +190,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T
 #pragma unroll
         for (int i = 0; i < kBV; ++i) {
             const int q = i * kPassThreads + tid;
-            if (q < nvec) cp_async16(&buf[swz(q >> 3, q & 7)], &p.u[gidx(base, q)]);
+            if (q < nvec) cp_async16(&buf[q], &p.u[gidx(base, q)]);
         }
     };
     auto issue_s = [&](long long t) {
         const uint64_t base = tile_base(t);
 #pragma unroll
-        for (int v = 0; v < kBV; ++v) {
-            const int q = tid * kBV + v;
+        for (int i = 0; i < kBV; ++i) {
+            const int q = i * kPassThreads + tid;
             if (q < nvec) cp_async16(&S[q], &p.stream[gidx(base, q)]);
         }
     };
@@ -231,8 +226,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T
         if (p.first) build_tab(t, tab0);
     }
     int stage = 0;
-    const int blk = tid;
-    const bool active = (blk * kBV) < nvec;
+    // vectors of this thread that exist in a tile (small chains have tiles < 4096 vectors)
+    const int nmine = tid < nvec ? ((nvec - 1 - tid) / kPassThreads + 1 < kBV ? (nvec - 1 - tid) / kPassThreads + 1 : kBV)
+                                 : 0;
     for (; t < p.ntiles; t += gridDim.x, stage ^= 1) {
         const long long tn = t + gridDim.x;
         V *Ucur = stage ? U1 : U0;
@@ -249,93 +245,97 @@ __global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T
 
         const uint64_t base = tile_base(t);
         T pd0 = 0, pd1 = 0, pn = 0;
-        if (active) {
-            C self[BE], r[BE];
+        C self[kBV * VE], r[kBV * VE];
 #pragma unroll
-            for (int v = 0; v < kBV; ++v) unpack(Ucur[swz(blk, v)], &self[v * VE]);
+        for (int i = 0; i < kBV; ++i) {
+            if (i < nmine) unpack(Ucur[i * kPassThreads + tid], &self[i * VE]);
+            else unpack(V{}, &self[i * VE]);
+        }
 #pragma unroll
-            for (int e = 0; e < BE; ++e) r[e] = C{(T)0, (T)0};
-            // flips of bits inside the register block
+        for (int e = 0; e < kBV * VE; ++e) r[e] = C{(T)0, (T)0};
+        int k0 = 0;
+        if (VE == 2 && p.c == 0) {
+            // bit 0 lives inside the 16-byte vector
+            const T f = p.hb[p.o];
 #pragma unroll
-            for (int lb = 0; lb < BLOG; ++lb) {
-                if (lb >= p.c && lb < tbits) {
-                    const T f = p.hb[p.o + lb - p.c];
-#pragma unroll
-                    for (int e = 0; e < BE; ++e) cfma(f, self[e ^ (1 << lb)], r[e]);
-                }
+            for (int i = 0; i < kBV; ++i) {
+                cfma(f, self[i * VE + VE - 1], r[i * VE]);
+                cfma(f, self[i * VE], r[i * VE + VE - 1]);
             }
-            // flips of bits across register blocks (neighbour block in shared memory)
-            const int k0 = (p.c > BLOG ? p.c : BLOG);
-            for (int lb = k0; lb < tbits; ++lb) {
-                const T f = p.hb[p.o + lb - p.c];
-                const int nb = blk ^ (1 << (lb - BLOG));
+            k0 = 1;
+        }
+        for (int k = k0; k < p.g; ++k) {
+            const T f = p.hb[p.o + k];
+            const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
-                for (int v = 0; v < kBV; ++v) {
+            for (int i = 0; i < kBV; ++i) {
+                if (i < nmine) {
                     C x[VE];
-                    unpack(Ucur[swz(nb, v)], x);
+                    unpack(Ucur[(i * kPassThreads + tid) ^ flip], x);
 #pragma unroll
-                    for (int e = 0; e < VE; ++e) cfma(f, x[e], r[v * VE + e]);
+                    for (int e = 0; e < VE; ++e) cfma(f, x[e], r[i * VE + e]);
                 }
             }
-            if (p.first) {
-                // diagonal: E(b) - a on the 16 (8) amplitudes of this block
-                const int li0 = blk * BE;
-                const int tmask = (1 << p.ta) - 1;
+        }
+        if (p.first) {
+            const int tmask = (1 << p.ta) - 1;
 #pragma unroll
-                for (int e = 0; e < BE; ++e) {
-                    const int li = li0 + e;
-                    const T E = __ldg(&p.Ell[li]) + tcur[li & tmask] + tcur[64 + (li >> p.ta)] - aT;
-                    cfma(E, self[e], r[e]);
-                }
-            }
-            if (has_stream) {
-                cp_async_wait<1>();  // this thread's stream copies of tile t have landed
+            for (int i = 0; i < kBV; ++i) {
+                if (i < nmine) {
 #pragma unroll
-                for (int v = 0; v < kBV; ++v) {
-                    C x[VE];
-                    unpack(S[blk * kBV + v], x);
-#pragma unroll
-                    for (int e = 0; e < VE; ++e) cfma(bsT, x[e], r[v * VE + e]);
-                }
-            }
-            if (!p.last) {
-#pragma unroll
-                for (int v = 0; v < kBV; ++v)
-                    if (blk * kBV + v < nvec) p.out[gidx(base, blk * kBV + v)] = pack(&r[v * VE]);
-            } else if (p.epilogue == EPI_ENERGY) {
-#pragma unroll
-                for (int e = 0; e < BE; ++e) {
-                    if (((blk * BE + e) >> LOGVE) < nvec) {
-                        pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
-                        pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
-                        pn = fma(self[e].x, self[e].x, fma(self[e].y, self[e].y, pn));
+                    for (int e = 0; e < VE; ++e) {
+                        const int li = ((i * kPassThreads + tid) << LOGVE) + e;
+                        const T E = __ldg(&p.Ell[li]) + tcur[li & tmask] + tcur[64 + (li >> p.ta)] - aT;
+                        cfma(E, self[i * VE + e], r[i * VE + e]);
                     }
                 }
-            } else {
+            }
+        }
+        if (has_stream) {
+            cp_async_wait<1>();  // this thread's stream copies of tile t have landed
 #pragma unroll
-                for (int e = 0; e < BE; ++e) {
-                    r[e].x *= svT;
-                    r[e].y *= svT;
+            for (int i = 0; i < kBV; ++i) {
+                if (i < nmine) {
+                    C x[VE];
+                    unpack(S[i * kPassThreads + tid], x);
+#pragma unroll
+                    for (int e = 0; e < VE; ++e) cfma(bsT, x[e], r[i * VE + e]);
                 }
+            }
+        }
+        if (!p.last) {
 #pragma unroll
-                for (int v = 0; v < kBV; ++v)
-                    if (blk * kBV + v < nvec) st_stream(&p.out[gidx(base, blk * kBV + v)], pack(&r[v * VE]));
-                if (p.epilogue == EPI_KRYLOV) {
+            for (int i = 0; i < kBV; ++i)
+                if (i < nmine) p.out[gidx(base, i * kPassThreads + tid)] = pack(&r[i * VE]);
+        } else if (p.epilogue == EPI_ENERGY) {
 #pragma unroll
-                    for (int e = 0; e < BE; ++e) {
-                        if (((blk * BE + e) >> LOGVE) < nvec) {
-                            pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
-                            pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
-                            pn = fma(r[e].x, r[e].x, fma(r[e].y, r[e].y, pn));
-                        }
-                    }
+            for (int e = 0; e < kBV * VE; ++e) {
+                pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
+                pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
+                pn = fma(self[e].x, self[e].x, fma(self[e].y, self[e].y, pn));
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < kBV * VE; ++e) {
+                r[e].x *= svT;
+                r[e].y *= svT;
+            }
+#pragma unroll
+            for (int i = 0; i < kBV; ++i)
+                if (i < nmine) st_stream(&p.out[gidx(base, i * kPassThreads + tid)], pack(&r[i * VE]));
+            if (p.epilogue == EPI_KRYLOV) {
+#pragma unroll
+                for (int e = 0; e < kBV * VE; ++e) {
+                    pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
+                    pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
+                    pn = fma(r[e].x, r[e].x, fma(r[e].y, r[e].y, pn));
                 }
             }
         }
         acc_d0 += (double)pd0;
         acc_d1 += (double)pd1;
         acc_n += (double)pn;
-        if (has_stream && tn < p.ntiles && active) issue_s(tn);
+        if (has_stream && tn < p.ntiles) issue_s(tn);
         cp_async_commit();
     }
     cp_async_wait<0>();
