@@ -123,7 +123,10 @@ osmps_status osmps_ed_download(osmps_ed_t *ed, void *dst_host, const void *src_d
 
 /*
  * out <- H psi, matrix-free (Sec. III.D, rule set times psi; Eq. OKrylov).
- * psi, out: device buffers of D elements, must not alias.  No sync.
+ * psi, out: device buffers of D elements, must not alias.  No sync.  The
+ * kernels' internal waits are bounded; if one gives up, the next call of this
+ * handle that synchronises (energy, Lanczos, Krylov, timing_read) returns
+ * OSMPS_ETIMEOUT.
  */
 osmps_status osmps_ed_apply_H(osmps_ed_t *ed, const void *psi, void *out);
 

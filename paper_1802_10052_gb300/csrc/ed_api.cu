@@ -113,6 +113,18 @@ osmps_status read_scalars(Handle *h, size_t off, size_t bytes) {
 
 #define CTL_OFF(f) offsetof(KrylovCtl, f)
 
+// Synchronise and report (then clear) a bounded device wait that gave up.
+osmps_status sync_and_check(Handle *h) {
+    CK(cudaStreamSynchronize(h->stream));
+    int e = 0;
+    CK(cudaMemcpy(&e, &h->ctl->error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        CK(cudaMemset(&h->ctl->error, 0, sizeof(int)));
+        return OSMPS_ETIMEOUT;
+    }
+    return OSMPS_OK;
+}
+
 __global__ void ctl_init_kernel(KrylovCtl *ctl, double bd_tol) {
     ctl->bd_tol = bd_tol;
     ctl->err_sum = 0.0;
@@ -289,6 +301,7 @@ osmps_status osmps_ed_timing_enable(osmps_ed_t *ed, int enable) {
 osmps_status osmps_ed_timing_read(osmps_ed_t *ed, double *hpsi_ms, int64_t *hpsi_calls, int reset) {
     if (ed == nullptr) return OSMPS_EINVAL;
     CKS(timing_flush(&ed->h));
+    CKS(sync_and_check(&ed->h));
     if (hpsi_ms) *hpsi_ms = ed->h.t_ms;
     if (hpsi_calls) *hpsi_calls = ed->h.t_calls;
     if (reset) {
@@ -357,7 +370,9 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
         // per-CTA partials: 4 doubles per CTA for every streaming kernel; the
         // multi-dot of the Gram-Schmidt pass needs 2 per vector per CTA
         const size_t g = (size_t)hd->nsm * 8;
-        hd->partials_cap = g * 4;
+        // H.psi writes 4 doubles per consumer warp of each persistent CTA
+        const size_t gh = (size_t)hd->nsm * 2 * hpsi_partials_per_cta();
+        hd->partials_cap = (gh > g ? gh : g) * 4;
         hd->partials = (double *)dev_alloc(hd, sizeof(double) * hd->partials_cap, &err);
         if (err != cudaSuccess) break;
         const size_t zneed = (g + 1) * ((size_t)(L * L + L + 1) + 4096);
@@ -492,6 +507,7 @@ osmps_status osmps_ed_energy(osmps_ed_t *ed, const void *psi, double *e_num, dou
     h->launches += 1;
     CK(cudaGetLastError());
     CKS(read_scalars(h, CTL_OFF(work) + 3 * sizeof(double), 2 * sizeof(double)));
+    CKS(sync_and_check(h));
     if (e_num) *e_num = h->ctl_host->work[3];
     if (norm2) *norm2 = h->ctl_host->work[4];
     return OSMPS_OK;
@@ -522,6 +538,7 @@ osmps_status osmps_ed_krylov_evolve(osmps_ed_t *ed, void *psi, double dt, int ns
         CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, m));
     }
     CKS(read_scalars(h, CTL_OFF(err_sum), sizeof(double)));
+    CKS(sync_and_check(h));
     if (err_estimate) *err_estimate = h->ctl_host->err_sum;
     return OSMPS_OK;
 }
@@ -585,7 +602,7 @@ osmps_status osmps_ed_lanczos_ground(osmps_ed_t *ed, void *psi, double tol, int 
         }
         if (breakdown) break;
     }
-    CK(cudaStreamSynchronize(h->stream));
+    CKS(sync_and_check(h));
     if (energy) *energy = best_e;
     if (residual) *residual = best_res;
     if (iters) *iters = done_iters;

@@ -37,7 +37,7 @@ struct KrylovCtl {
     double epi2[3];                   // epilogue scalars of the ground-state residual pass
     double bd_tol;                    // relative breakdown threshold
     int m_eff;                        // vectors in the basis (< m after breakdown)
-    int pad;
+    int error;                        // raised by a kernel whose bounded wait gave up
     double work[7 * kMaxLanczos];     // scratch of the single-thread tridiagonal solves
 };
 
@@ -84,6 +84,7 @@ cudaError_t build_tables(Handle *h);
 cudaError_t launch_hpsi(Handle *h, const HpsiArgs &a, int *nparts_out);
 cudaError_t launch_hpsi_timed(Handle *h, const HpsiArgs &a, int *nparts_out);
 int hpsi_grid(Handle *h, int pass);
+int hpsi_partials_per_cta();
 
 // vec_kernels.cu
 cudaError_t launch_fill_basis(Handle *h, void *psi, uint64_t b);

@@ -25,6 +25,7 @@
 //       w = sv*H u - a*sv*u - b*uprev
 //   and the inner products <sv u, w> and |w|^2 (FP32 per thread and tile,
 //   FP64 across tiles and CTAs, fixed reduction order).
+#include <cuda.h>  // CUtensorMap types; the encoder is fetched through the runtime's driver entry point
 #include <cuda_runtime.h>
 
 #include "ed_internal.h"
@@ -47,24 +48,30 @@ template <> struct Cx<double> {
     static constexpr int BLOG = 3;
 };
 
-constexpr int kBV = 8;                                  // 16-byte vectors per register block
+constexpr int kBV = 8;                                  // 16-byte vectors per consumer thread per tile
+constexpr int kHB = kBV / 2;                            // processed in two halves
 constexpr int kTileV = 1 << (kTileBytesLog2 - 4);       // 16-byte vectors per tile
 constexpr int kTab = 256;                               // TA (<= 64) + TB (<= 128) per stage
-static_assert(kTileV == kBV * kPassThreads, "eight vectors per thread per tile");
+constexpr int kStages = 3;                              // shared-memory ring of tiles
+constexpr int kConsumerWarps = kPassThreads / 32;       // 16
+constexpr int kHpsiThreads = kPassThreads + 32;         // + one producer warp
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
+static_assert(kTileV == kBV * kPassThreads, "eight vectors per consumer thread per tile");
 
 template <typename T>
 struct PassParams {
-    const typename Cx<T>::v16 *u;       // vector being multiplied (tile staged in shared memory)
     const typename Cx<T>::v16 *stream;  // elementwise input: previous Lanczos vector (first pass) or partial sum
     typename Cx<T>::v16 *out;
     const T *Ell;
     const T *Fhh;
     const double *epi;                  // sv, a, b (device) or null
-    double *partials;
+    double *partials;                   // 4 doubles per consumer warp
     const int *m_eff;
+    int *err;                           // set to 1 when a bounded wait gives up
     long long ntiles;
     int stop_index;
-    int L, c, o, g, ta, first, last, epilogue;
+    int L, c, o, g, ta, first, last, epilogue, rank;
+    unsigned tile_bytes;
     T hb[kMaxL + 1];
 };
 
@@ -90,75 +97,115 @@ __device__ __forceinline__ void cfma(double f, const double2 &x, double2 &acc) {
     acc.y = fma(f, x.y, acc.y);
 }
 
+// ---- mbarrier / TMA primitives (PTX) ----
+__device__ __forceinline__ unsigned smem_u32(const void *ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity; gives up after kWaitNs or when
+// another thread has already raised the error flag.
+__device__ __noinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, const int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile const int *)err != 0) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *tm, int rank, const int *crd,
+                                         unsigned long long *bar) {
+    const unsigned long long tmp = reinterpret_cast<unsigned long long>(tm);
+    if (rank == 3) {
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(smem_u32(dst)),
+            "l"(tmp), "r"(crd[0]), "r"(crd[1]), "r"(crd[2]), "r"(smem_u32(bar))
+            : "memory");
+    } else {
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+            "l"(tmp), "r"(crd[0]), "r"(crd[1]), "r"(crd[2]), "r"(crd[3]), "r"(crd[4]), "r"(smem_u32(bar))
+            : "memory");
+    }
+}
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap *tm, int rank, const int *crd) {
+    const unsigned long long tmp = reinterpret_cast<unsigned long long>(tm);
+    if (rank == 3) {
+        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(tmp), "r"(crd[0]),
+                     "r"(crd[1]), "r"(crd[2])
+                     : "memory");
+    } else {
+        asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"(tmp),
+                     "r"(crd[0]), "r"(crd[1]), "r"(crd[2]), "r"(crd[3]), "r"(crd[4])
+                     : "memory");
+    }
+}
+
 template <typename V>
-__device__ __forceinline__ void st_stream(V *p, const V &v) {
-    __stcs(p, v);
+__device__ __forceinline__ void st_stream(V *ptr, const V &v) {
+    __stcs(ptr, v);
 }
 
+// One pass of the product, warp-specialized and persistent (one CTA per SM):
+//  * warp 16 (producer) fills a 3-stage shared-memory ring with tiles of u by
+//    TMA (cp.async.bulk.tensor, completion on the stage's "full" mbarrier),
+//    prefetches the matching tile of the elementwise stream into L2, and in
+//    the first pass builds the tile's diagonal tables;
+//  * warps 0..15 (consumers) wait on "full", form the flips, diagonal,
+//    stream term and epilogue for the vectors q = tid + 512 i they own (all
+//    global stores lane-coalesced), then release the stage on "empty".
+// All waits are bounded (2 s); on timeout the error flag is raised, the
+// producer drains the copies it issued, and the kernel returns.
 template <typename T>
-__device__ __forceinline__ void block_reduce3(double v0, double v1, double v2, double *dst) {
-    __shared__ double red[3][kPassThreads / 32];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, off);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        red[0][w] = v0;
-        red[1][w] = v1;
-        red[2][w] = v2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s0 = 0, s1 = 0, s2 = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            s0 += red[0][i];
-            s1 += red[1][i];
-            s2 += red[2][i];
-        }
-        dst[0] = s0;
-        dst[1] = s1;
-        dst[2] = s2;
-        dst[3] = 0.0;
-    }
-}
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// One pass of the product.  Persistent: one 512-thread CTA per SM walks the
-// tiles.  Thread tid owns the 16-byte vectors q = tid + 512 i (i < 8) of every
-// tile, so all global loads and stores are lane-coalesced.  The tile of u for
-// the next iteration is copied asynchronously into the second shared-memory
-// stage while the current one is computed; the elementwise stream (previous
-// vector or partial sum) of the thread's own vectors is copied one tile ahead
-// by the thread that consumes it.
-template <typename T>
-__global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T> p) {
+__global__ void __launch_bounds__(kHpsiThreads, 1)
+    hpsi_pass_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
+                     PassParams<T> p) {
     typedef typename Cx<T>::c C;
     typedef typename Cx<T>::v16 V;
     constexpr int VE = Cx<T>::VE;
     constexpr int LOGVE = Cx<T>::LOGVE;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *U0 = reinterpret_cast<V *>(smem_raw);
-    V *U1 = U0 + kTileV;
-    V *S = U1 + kTileV;
-    T *tab0 = reinterpret_cast<T *>(S + kTileV);
-    T *tab1 = tab0 + kTab;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    V *U = reinterpret_cast<V *>(smem_raw);
+    T *tab = reinterpret_cast<T *>(U + kStages * kTileV);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(tab + kStages * kTab);
+    unsigned long long *empty = full + kStages;
 
     if (p.m_eff != nullptr && *p.m_eff <= p.stop_index) return;
 
-    const int tid = threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
     const int tbits = p.c + p.g;
     const int nvec = (1 << tbits) >> LOGVE;
     const uint64_t cmask = (1ull << p.c) - 1ull;
@@ -166,6 +213,73 @@ __global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T
     const uint64_t ocmask = (1ull << oc) - 1ull;
     const bool has_stream = p.stream != nullptr;
 
+    auto coords = [&](long long t, int *crd) {
+        if (p.rank == 3) {
+            crd[0] = 0;
+            crd[1] = 0;
+            crd[2] = (int)t;
+        } else {
+            crd[0] = 0;
+            crd[1] = (int)(t & (long long)ocmask);
+            crd[2] = 0;
+            crd[3] = 0;
+            crd[4] = (int)(t >> oc);
+        }
+    };
+
+    if (warp == kConsumerWarps) {
+        // ------------------------------ producer ------------------------------
+        long long n = 0;
+        for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++n) {
+            const int s = (int)(n % kStages);
+            const unsigned ph = (unsigned)((n / kStages) & 1);
+            if (n >= kStages) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(&empty[s], ph ^ 1u, p.err);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) {
+                    if (lane == 0) atomicExch(p.err, 1);
+                    break;
+                }
+            }
+            if (p.first) {
+                // diagonal tables of tile t: TA[x] = E_hh + sum_{j<ta} s_j(x) F_j, TB[y] = sum s_j(y) F_{ta+j}
+                const int a = p.g, ta = p.ta, tb = a - ta;
+                const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
+                T *tb_s = tab + s * kTab;
+                for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
+                    if (x < (1 << ta)) {
+                        T v = F[a];
+                        for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
+                        tb_s[x] = v;
+                    } else {
+                        const int y = x - (1 << ta);
+                        T v = (T)0;
+                        for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
+                        tb_s[64 + y] = v;
+                    }
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                int crd[5];
+                coords(t, crd);
+                mbar_arrive_expect_tx(&full[s], p.tile_bytes);
+                tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &full[s]);
+                if (has_stream) tma_prefetch_l2(&tm_s, p.rank, crd);
+            }
+        }
+        // drain: every copy this CTA issued has landed before it exits
+        if (lane == 0) {
+            const long long first = n > kStages ? n - kStages : 0;
+            for (long long k = first; k < n; ++k)
+                mbar_wait(&full[(int)(k % kStages)], (unsigned)((k / kStages) & 1), p.err);
+        }
+        return;
+    }
+
+    // ------------------------------ consumers ------------------------------
+    const int tid = threadIdx.x;
     double sv = 1.0, ea = 0.0, eb = 0.0;
     if (p.epi != nullptr) {
         sv = p.epi[0];
@@ -176,172 +290,152 @@ __global__ void __launch_bounds__(kPassThreads, 1) hpsi_pass_kernel(PassParams<T
     const T aT = (T)ea;
     const T bsT = (p.first && has_stream) ? (T)(-eb / sv) : (T)1;
     const T svT = (T)sv;
-
-    auto tile_base = [&](long long t) -> uint64_t {
-        const uint64_t tt = (uint64_t)t;
-        return ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
-    };
+    const int nmine =
+        tid < nvec ? ((nvec - 1 - tid) / kPassThreads + 1 < kBV ? (nvec - 1 - tid) / kPassThreads + 1 : kBV) : 0;
     auto gidx = [&](uint64_t base, int q) -> uint64_t {  // global 16-byte vector index of tile vector q
         const int li = q << LOGVE;
         return (base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask)) >> LOGVE;
     };
-    auto issue_u = [&](long long t, V *buf) {
-        const uint64_t base = tile_base(t);
-#pragma unroll
-        for (int i = 0; i < kBV; ++i) {
-            const int q = i * kPassThreads + tid;
-            if (q < nvec) cp_async16(&buf[q], &p.u[gidx(base, q)]);
-        }
-    };
-    auto issue_s = [&](long long t) {
-        const uint64_t base = tile_base(t);
-#pragma unroll
-        for (int i = 0; i < kBV; ++i) {
-            const int q = i * kPassThreads + tid;
-            if (q < nvec) cp_async16(&S[q], &p.stream[gidx(base, q)]);
-        }
-    };
-    auto build_tab = [&](long long t, T *tab) {
-        const int a = p.g, ta = p.ta, tb = a - ta;
-        const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
-        if (tid < (1 << ta)) {
-            T s = F[a];
-            for (int j = 0; j < ta; ++j) s += ((tid >> j) & 1) ? -F[j] : F[j];
-            tab[tid] = s;
-        } else if (tid < (1 << ta) + (1 << tb)) {
-            const int y = tid - (1 << ta);
-            T s = (T)0;
-            for (int j = 0; j < tb; ++j) s += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
-            tab[64 + y] = s;
-        }
-    };
 
     double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
-    long long t = blockIdx.x;
-    if (t < p.ntiles) {
-        issue_u(t, U0);
-        cp_async_commit();
-        if (has_stream) issue_s(t);
-        cp_async_commit();
-        if (p.first) build_tab(t, tab0);
-    }
-    int stage = 0;
-    // vectors of this thread that exist in a tile (small chains have tiles < 4096 vectors)
-    const int nmine = tid < nvec ? ((nvec - 1 - tid) / kPassThreads + 1 < kBV ? (nvec - 1 - tid) / kPassThreads + 1 : kBV)
-                                 : 0;
-    for (; t < p.ntiles; t += gridDim.x, stage ^= 1) {
-        const long long tn = t + gridDim.x;
-        V *Ucur = stage ? U1 : U0;
-        V *Unext = stage ? U0 : U1;
-        T *tcur = stage ? tab1 : tab0;
-        T *tnext = stage ? tab0 : tab1;
-        cp_async_wait<1>();
-        __syncthreads();
-        if (tn < p.ntiles) {
-            issue_u(tn, Unext);
-            if (p.first) build_tab(tn, tnext);
+    long long n = 0;
+    for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++n) {
+        const int s = (int)(n % kStages);
+        const unsigned ph = (unsigned)((n / kStages) & 1);
+        const V *Ucur = U + (size_t)s * kTileV;
+        const T *tcur = tab + s * kTab;
+        const uint64_t tt = (uint64_t)t;
+        const uint64_t base = ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
+        if (!mbar_wait(&full[s], ph, p.err)) {
+            atomicExch(p.err, 1);
+            break;
         }
-        cp_async_commit();
-
-        const uint64_t base = tile_base(t);
         T pd0 = 0, pd1 = 0, pn = 0;
-        C self[kBV * VE], r[kBV * VE];
+        // two halves of four vectors keep the live registers low
+        C self[2][kHB * VE], r[2][kHB * VE];
 #pragma unroll
-        for (int i = 0; i < kBV; ++i) {
-            if (i < nmine) unpack(Ucur[i * kPassThreads + tid], &self[i * VE]);
-            else unpack(V{}, &self[i * VE]);
-        }
+        for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
-        for (int e = 0; e < kBV * VE; ++e) r[e] = C{(T)0, (T)0};
-        int k0 = 0;
-        if (VE == 2 && p.c == 0) {
-            // bit 0 lives inside the 16-byte vector
-            const T f = p.hb[p.o];
-#pragma unroll
-            for (int i = 0; i < kBV; ++i) {
-                cfma(f, self[i * VE + VE - 1], r[i * VE]);
-                cfma(f, self[i * VE], r[i * VE + VE - 1]);
+            for (int i = 0; i < kHB; ++i) {
+                const int ii = hh * kHB + i;
+                if (ii < nmine) unpack(Ucur[ii * kPassThreads + tid], &self[hh][i * VE]);
+                else unpack(V{}, &self[hh][i * VE]);
             }
-            k0 = 1;
-        }
-        for (int k = k0; k < p.g; ++k) {
-            const T f = p.hb[p.o + k];
-            const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
-            for (int i = 0; i < kBV; ++i) {
-                if (i < nmine) {
-                    C x[VE];
-                    unpack(Ucur[(i * kPassThreads + tid) ^ flip], x);
+            for (int e = 0; e < kHB * VE; ++e) r[hh][e] = C{(T)0, (T)0};
+            int k0 = 0;
+            if (VE == 2 && p.c == 0) {
+                // bit 0 lives inside the 16-byte vector
+                const T f = p.hb[p.o];
 #pragma unroll
-                    for (int e = 0; e < VE; ++e) cfma(f, x[e], r[i * VE + e]);
+                for (int i = 0; i < kHB; ++i) {
+                    cfma(f, self[hh][i * VE + VE - 1], r[hh][i * VE]);
+                    cfma(f, self[hh][i * VE], r[hh][i * VE + VE - 1]);
                 }
+                k0 = 1;
             }
-        }
-        if (p.first) {
-            const int tmask = (1 << p.ta) - 1;
+            for (int k = k0; k < p.g; ++k) {
+                const T f = p.hb[p.o + k];
+                const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
-            for (int i = 0; i < kBV; ++i) {
-                if (i < nmine) {
+                for (int i = 0; i < kHB; ++i) {
+                    const int ii = hh * kHB + i;
+                    if (ii < nmine) {
+                        C x[VE];
+                        unpack(Ucur[(ii * kPassThreads + tid) ^ flip], x);
 #pragma unroll
-                    for (int e = 0; e < VE; ++e) {
-                        const int li = ((i * kPassThreads + tid) << LOGVE) + e;
-                        const T E = __ldg(&p.Ell[li]) + tcur[li & tmask] + tcur[64 + (li >> p.ta)] - aT;
-                        cfma(E, self[i * VE + e], r[i * VE + e]);
+                        for (int e = 0; e < VE; ++e) cfma(f, x[e], r[hh][i * VE + e]);
                     }
                 }
             }
-        }
-        if (has_stream) {
-            cp_async_wait<1>();  // this thread's stream copies of tile t have landed
+            if (p.first) {
+                const int tmask = (1 << p.ta) - 1;
 #pragma unroll
-            for (int i = 0; i < kBV; ++i) {
-                if (i < nmine) {
-                    C x[VE];
-                    unpack(S[i * kPassThreads + tid], x);
+                for (int i = 0; i < kHB; ++i) {
+                    const int ii = hh * kHB + i;
+                    if (ii < nmine) {
 #pragma unroll
-                    for (int e = 0; e < VE; ++e) cfma(bsT, x[e], r[i * VE + e]);
+                        for (int e = 0; e < VE; ++e) {
+                            const int li = ((ii * kPassThreads + tid) << LOGVE) + e;
+                            const T E = __ldg(&p.Ell[li]) + tcur[li & tmask] + tcur[64 + (li >> p.ta)] - aT;
+                            cfma(E, self[hh][i * VE + e], r[hh][i * VE + e]);
+                        }
+                    }
                 }
             }
-        }
-        if (!p.last) {
-#pragma unroll
-            for (int i = 0; i < kBV; ++i)
-                if (i < nmine) p.out[gidx(base, i * kPassThreads + tid)] = pack(&r[i * VE]);
-        } else if (p.epilogue == EPI_ENERGY) {
-#pragma unroll
-            for (int e = 0; e < kBV * VE; ++e) {
-                pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
-                pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
-                pn = fma(self[e].x, self[e].x, fma(self[e].y, self[e].y, pn));
+            if (hh == 1) {
+                // stage s is no longer read by this warp
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
             }
-        } else {
+            if (has_stream) {
 #pragma unroll
-            for (int e = 0; e < kBV * VE; ++e) {
-                r[e].x *= svT;
-                r[e].y *= svT;
+                for (int i = 0; i < kHB; ++i) {
+                    const int ii = hh * kHB + i;
+                    if (ii < nmine) {
+                        C x[VE];
+                        unpack(__ldcs(&p.stream[gidx(base, ii * kPassThreads + tid)]), x);
+#pragma unroll
+                        for (int e = 0; e < VE; ++e) cfma(bsT, x[e], r[hh][i * VE + e]);
+                    }
+                }
             }
+            if (!p.last) {
 #pragma unroll
-            for (int i = 0; i < kBV; ++i)
-                if (i < nmine) st_stream(&p.out[gidx(base, i * kPassThreads + tid)], pack(&r[i * VE]));
-            if (p.epilogue == EPI_KRYLOV) {
+                for (int i = 0; i < kHB; ++i) {
+                    const int ii = hh * kHB + i;
+                    if (ii < nmine) p.out[gidx(base, ii * kPassThreads + tid)] = pack(&r[hh][i * VE]);
+                }
+            } else if (p.epilogue == EPI_ENERGY) {
 #pragma unroll
-                for (int e = 0; e < kBV * VE; ++e) {
-                    pd0 = fma(self[e].x, r[e].x, fma(self[e].y, r[e].y, pd0));
-                    pd1 = fma(self[e].x, r[e].y, fma(-self[e].y, r[e].x, pd1));
-                    pn = fma(r[e].x, r[e].x, fma(r[e].y, r[e].y, pn));
+                for (int e = 0; e < kHB * VE; ++e) {
+                    const C &u = self[hh][e], &w = r[hh][e];
+                    pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
+                    pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
+                    pn = fma(u.x, u.x, fma(u.y, u.y, pn));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kHB * VE; ++e) {
+                    r[hh][e].x *= svT;
+                    r[hh][e].y *= svT;
+                }
+#pragma unroll
+                for (int i = 0; i < kHB; ++i) {
+                    const int ii = hh * kHB + i;
+                    if (ii < nmine) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], pack(&r[hh][i * VE]));
+                }
+                if (p.epilogue == EPI_KRYLOV) {
+#pragma unroll
+                    for (int e = 0; e < kHB * VE; ++e) {
+                        const C &u = self[hh][e], &w = r[hh][e];
+                        pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
+                        pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
+                        pn = fma(w.x, w.x, fma(w.y, w.y, pn));
+                    }
                 }
             }
         }
         acc_d0 += (double)pd0;
         acc_d1 += (double)pd1;
         acc_n += (double)pn;
-        if (has_stream && tn < p.ntiles) issue_s(tn);
-        cp_async_commit();
     }
-    cp_async_wait<0>();
 
     if (p.last && p.epilogue != EPI_PLAIN && p.partials != nullptr) {
-        block_reduce3<T>(acc_d0 * sv, acc_d1 * sv, acc_n, p.partials + 4 * (size_t)blockIdx.x);
+        // per-warp partials (fixed order, no CTA barrier so early exits cannot hang)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            acc_d0 += __shfl_xor_sync(0xffffffffu, acc_d0, off);
+            acc_d1 += __shfl_xor_sync(0xffffffffu, acc_d1, off);
+            acc_n += __shfl_xor_sync(0xffffffffu, acc_n, off);
+        }
+        if (lane == 0) {
+            double *dst = p.partials + 4 * ((size_t)blockIdx.x * kConsumerWarps + warp);
+            dst[0] = acc_d0 * sv;
+            dst[1] = acc_d1 * sv;
+            dst[2] = acc_n;
+            dst[3] = 0.0;
+        }
     }
 }
 
@@ -393,9 +487,9 @@ __global__ void fhh_table_kernel(T *Fhh, int L, int a1, const double *Jr, long l
 PassPlan make_plan(int L, int prec) {
     PassPlan pl{};
     const int logE = (prec == OSMPS_FP64) ? 4 : 3;       // log2 bytes per amplitude
-    const int TB = kTileBytesLog2 - logE;                  // tile bits
-    const int cdef = kChunkBytesLog2 - logE;               // 128-byte chunk
-    const int cmin = 5 - logE;                             // 32-byte sector
+    const int TB = kTileBytesLog2 - logE;                  // tile bits (64 KiB tile)
+    const int cmin = 5 - logE;                             // chunk >= one 32-byte sector
+    const int cmax = 11 - logE;                            // chunk <= 256 eight-byte words (TMA box)
     pl.a1 = L < TB ? L : TB;
     pl.ta = pl.a1 / 2;
     pl.p[0] = PassDesc{0, 0, pl.a1, 1, 1ll << (L - pl.a1)};
@@ -404,13 +498,15 @@ PassPlan make_plan(int L, int prec) {
     if (rest > 0) {
         const int room = TB - cmin;
         const int k = (rest + room - 1) / room;
-        int gmax = (rest + k - 1) / k;
-        int c = cdef < TB - gmax ? cdef : TB - gmax;
-        if (c < cmin) c = cmin;
         int o = pl.a1;
         int left = rest;
         for (int i = 0; i < k; ++i) {
             const int g = (left + (k - i) - 1) / (k - i);
+            // fill the tile: carry as many contiguous low bits as fit
+            int c = TB - g;
+            if (c > cmax) c = cmax;
+            if (c > pl.a1) c = pl.a1;
+            if (c < cmin) c = cmin;
             pl.p[pl.npass++] = PassDesc{c, o, g, 0, 1ll << (L - c - g)};
             o += g;
             left -= g;
@@ -419,7 +515,10 @@ PassPlan make_plan(int L, int prec) {
     return pl;
 }
 
-static size_t pass_smem() { return 3u * (1u << kTileBytesLog2) + 2 * kTab * sizeof(double); }
+static size_t pass_smem() {
+    return (size_t)kStages * (1u << kTileBytesLog2) + (size_t)kStages * kTab * sizeof(double) +
+           2 * kStages * sizeof(unsigned long long);
+}
 
 template <typename T>
 static int grid_for(Handle *h, long long ntiles) {
@@ -427,7 +526,7 @@ static int grid_for(Handle *h, long long ntiles) {
     if (occ < 0) {
         cudaFuncSetAttribute(hpsi_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem());
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hpsi_pass_kernel<T>, kPassThreads, pass_smem());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hpsi_pass_kernel<T>, kHpsiThreads, pass_smem());
         occ = n > 0 ? n : 1;
     }
     long long g = (long long)occ * h->nsm;
@@ -437,6 +536,78 @@ static int grid_for(Handle *h, long long ntiles) {
 int hpsi_grid(Handle *h, int pass) {
     const long long nt = h->plan.p[pass].ntiles;
     return h->prec == OSMPS_FP64 ? grid_for<double>(h, nt) : grid_for<float>(h, nt);
+}
+
+int hpsi_partials_per_cta() { return kConsumerWarps; }
+
+// ---- tensor maps ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)ptr;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map of the tiles of one pass over the vector at base (8-byte words).
+//  first pass : 3-D (256-word rows, rows per tile, tiles)
+//  later      : 5-D (chunk words, low other bits, low group bits, high group
+//               bits, high other bits); the box is one tile, landing in shared
+//               memory as local index (group << c) | chunk.
+static cudaError_t encode_pass_map(Handle *h, const PassDesc &d, const void *base, CUtensorMap *tm, int *rank) {
+    EncodeTiledFn enc = encoder();
+    if (enc == nullptr) return cudaErrorNotSupported;
+    const uint64_t e = h->esize / 8;  // words per amplitude
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    if (d.first) {
+        const uint64_t W = (1ull << d.g) * e;
+        const uint64_t d0 = W < 256 ? W : 256;
+        dims[0] = d0;
+        dims[1] = W / d0;
+        dims[2] = (cuuint64_t)d.ntiles;
+        strides[0] = d0 * 8;
+        strides[1] = W * 8;
+        box[0] = (cuuint32_t)d0;
+        box[1] = (cuuint32_t)(W / d0);
+        box[2] = 1;
+        *rank = 3;
+    } else {
+        const int g1 = d.g < 8 ? d.g : 8, g2 = d.g - g1;
+        const uint64_t X = (1ull << d.c) * e;
+        dims[0] = X;
+        dims[1] = 1ull << (d.o - d.c);
+        dims[2] = 1ull << g1;
+        dims[3] = 1ull << g2;
+        dims[4] = 1ull << (h->L - d.o - d.g);
+        strides[0] = (1ull << d.c) * h->esize;
+        strides[1] = (1ull << d.o) * h->esize;
+        strides[2] = (1ull << (d.o + g1)) * h->esize;
+        strides[3] = (1ull << (d.o + d.g)) * h->esize;
+        box[0] = (cuuint32_t)X;
+        box[1] = 1;
+        box[2] = 1u << g1;
+        box[3] = 1u << g2;
+        box[4] = 1;
+        *rank = 5;
+    }
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)*rank, const_cast<void *>(base), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -490,14 +661,25 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
             if (i > 0) src_acc = ((from_end + 1) % 2 == 0) ? a.out : a.tmp;
         }
         if (last && a.epilogue == EPI_ENERGY) dst = nullptr;
-        p.u = reinterpret_cast<const V *>(a.u);
-        p.stream = reinterpret_cast<const V *>(i == 0 ? a.uprev : src_acc);
+        const void *stream = (i == 0) ? a.uprev : src_acc;
+        CUtensorMap tm_u, tm_s;
+        int rank = 0, rank_s = 0;
+        cudaError_t err = encode_pass_map(h, d, a.u, &tm_u, &rank);
+        if (err != cudaSuccess) return err;
+        if (stream != nullptr) {
+            err = encode_pass_map(h, d, stream, &tm_s, &rank_s);
+            if (err != cudaSuccess) return err;
+        } else {
+            tm_s = tm_u;
+        }
+        p.stream = reinterpret_cast<const V *>(stream);
         p.out = reinterpret_cast<V *>(dst);
         p.Ell = reinterpret_cast<const T *>(h->Ell);
         p.Fhh = reinterpret_cast<const T *>(h->Fhh);
         p.epi = a.epi;
         p.partials = a.partials;
         p.m_eff = a.m_eff;
+        p.err = &h->ctl->error;
         p.stop_index = a.stop_index;
         p.ntiles = d.ntiles;
         p.L = h->L;
@@ -508,13 +690,15 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.first = d.first;
         p.last = last ? 1 : 0;
         p.epilogue = a.epilogue;
+        p.rank = rank;
+        p.tile_bytes = (unsigned)((1u << (d.c + d.g)) * h->esize);
         for (int k = 0; k <= kMaxL; ++k) p.hb[k] = (T)h->hbit[k];
         const int grid = grid_for<T>(h, d.ntiles);
-        hpsi_pass_kernel<T><<<grid, kPassThreads, pass_smem(), h->stream>>>(p);
+        hpsi_pass_kernel<T><<<grid, kHpsiThreads, pass_smem(), h->stream>>>(tm_u, tm_s, p);
         h->launches += 1;
-        cudaError_t err = cudaGetLastError();
+        err = cudaGetLastError();
         if (err != cudaSuccess) return err;
-        if (last) nparts = grid;
+        if (last) nparts = grid * kConsumerWarps;
     }
     if (nparts_out) *nparts_out = nparts;
     return cudaSuccess;
