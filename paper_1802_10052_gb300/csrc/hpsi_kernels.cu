@@ -54,7 +54,7 @@ constexpr int kTileV = 1 << (kTileBytesLog2 - 4);       // 16-byte vectors per t
 constexpr int kTab = 256;                               // TA (<= 64) + TB (<= 128) per stage
 constexpr int kStages = 3;                              // shared-memory ring of tiles
 constexpr int kConsumerWarps = kPassThreads / 32;       // 16
-constexpr int kHpsiThreads = kPassThreads + 32;         // + one producer warp
+constexpr int kHpsiThreads = kPassThreads;              // warp 0 also issues the copies
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 static_assert(kTileV == kBV * kPassThreads, "eight vectors per consumer thread per tile");
 
@@ -83,18 +83,24 @@ __device__ __forceinline__ float4 pack(const float2 *e) { return make_float4(e[0
 __device__ __forceinline__ void unpack(const double2 &v, double2 *e) { e[0] = v; }
 __device__ __forceinline__ double2 pack(const double2 *e) { return e[0]; }
 
-// acc += f * x on a complex amplitude: one packed FP32x2 FMA, or two FP64 FMAs
+// acc += f * x on a complex amplitude: one packed FP32x2 FMA (operands are
+// register pairs), or two FP64 FMAs
 __device__ __forceinline__ void cfma(float f, const float2 &x, float2 &acc) {
-    unsigned long long X = ((unsigned long long)__float_as_uint(x.y) << 32) | __float_as_uint(x.x);
-    unsigned long long F = ((unsigned long long)__float_as_uint(f) << 32) | __float_as_uint(f);
-    unsigned long long A = ((unsigned long long)__float_as_uint(acc.y) << 32) | __float_as_uint(acc.x);
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(A) : "l"(F), "l"(X));
-    acc.x = __uint_as_float((unsigned)A);
-    acc.y = __uint_as_float((unsigned)(A >> 32));
+    asm("{\n .reg .b64 a, m, v;\n mov.b64 a, {%0, %1};\n mov.b64 m, {%2, %2};\n mov.b64 v, {%3, %4};\n"
+        " fma.rn.f32x2 a, m, v, a;\n mov.b64 {%0, %1}, a;\n}\n"
+        : "+f"(acc.x), "+f"(acc.y)
+        : "f"(f), "f"(x.x), "f"(x.y));
 }
 __device__ __forceinline__ void cfma(double f, const double2 &x, double2 &acc) {
     acc.x = fma(f, x.x, acc.x);
     acc.y = fma(f, x.y, acc.y);
+}
+// acc += (f0, f1) * x elementwise on a pair of reals
+__device__ __forceinline__ void cfma2(float f0, float f1, const float2 &x, float2 &acc) {
+    asm("{\n .reg .b64 a, m, v;\n mov.b64 a, {%0, %1};\n mov.b64 m, {%2, %3};\n mov.b64 v, {%4, %5};\n"
+        " fma.rn.f32x2 a, m, v, a;\n mov.b64 {%0, %1}, a;\n}\n"
+        : "+f"(acc.x), "+f"(acc.y)
+        : "f"(f0), "f"(f1), "f"(x.x), "f"(x.y));
 }
 
 // ---- mbarrier / TMA primitives (PTX) ----
@@ -170,15 +176,16 @@ __device__ __forceinline__ void st_stream(V *ptr, const V &v) {
 }
 
 // One pass of the product, warp-specialized and persistent (one CTA per SM):
-//  * warp 16 (producer) fills a 3-stage shared-memory ring with tiles of u by
-//    TMA (cp.async.bulk.tensor, completion on the stage's "full" mbarrier),
-//    prefetches the matching tile of the elementwise stream into L2, and in
-//    the first pass builds the tile's diagonal tables;
-//  * warps 0..15 (consumers) wait on "full", form the flips, diagonal,
-//    stream term and epilogue for the vectors q = tid + 512 i they own (all
-//    global stores lane-coalesced), then release the stage on "empty".
-// All waits are bounded (2 s); on timeout the error flag is raised, the
-// producer drains the copies it issued, and the kernel returns.
+//  * a 3-stage shared-memory ring holds tiles of u, filled by TMA
+//    (cp.async.bulk.tensor, completion on the stage's "full" mbarrier); warp 0
+//    refills a stage as soon as all 16 warps have released it on its "empty"
+//    mbarrier, prefetches the matching tile of the elementwise stream into L2
+//    and, in the first pass, builds the tile's diagonal tables;
+//  * every warp waits on "full", forms the flips, diagonal, stream term and
+//    epilogue for the vectors q = tid + 512 i it owns (all global accesses
+//    lane-coalesced), then releases the stage.
+// All waits are bounded (2 s); on timeout the error flag is raised, warp 0
+// waits for the copies it issued, and the kernel returns.
 template <typename T>
 __global__ void __launch_bounds__(kHpsiThreads, 1)
     hpsi_pass_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
@@ -227,58 +234,51 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         }
     };
 
-    if (warp == kConsumerWarps) {
-        // ------------------------------ producer ------------------------------
-        long long n = 0;
-        for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++n) {
-            const int s = (int)(n % kStages);
-            const unsigned ph = (unsigned)((n / kStages) & 1);
-            if (n >= kStages) {
-                bool ok = true;
-                if (lane == 0) ok = mbar_wait(&empty[s], ph ^ 1u, p.err);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (!ok) {
-                    if (lane == 0) atomicExch(p.err, 1);
-                    break;
-                }
-            }
-            if (p.first) {
-                // diagonal tables of tile t: TA[x] = E_hh + sum_{j<ta} s_j(x) F_j, TB[y] = sum s_j(y) F_{ta+j}
-                const int a = p.g, ta = p.ta, tb = a - ta;
-                const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
-                T *tb_s = tab + s * kTab;
-                for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
-                    if (x < (1 << ta)) {
-                        T v = F[a];
-                        for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
-                        tb_s[x] = v;
-                    } else {
-                        const int y = x - (1 << ta);
-                        T v = (T)0;
-                        for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
-                        tb_s[64 + y] = v;
-                    }
-                }
-                __syncwarp();
-            }
-            if (lane == 0) {
-                int crd[5];
-                coords(t, crd);
-                mbar_arrive_expect_tx(&full[s], p.tile_bytes);
-                tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &full[s]);
-                if (has_stream) tma_prefetch_l2(&tm_s, p.rank, crd);
-            }
+    // Warp 0 issues the copies: tile n goes to stage n % kStages once all warps
+    // have released that stage's previous tile (n - kStages).
+    auto fill = [&](long long n, long long t) -> bool {
+        const int s = (int)(n % kStages);
+        if (n >= kStages) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&empty[s], (unsigned)(((n / kStages) & 1) ^ 1), p.err);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) return false;
         }
-        // drain: every copy this CTA issued has landed before it exits
+        if (p.first) {
+            // diagonal tables of tile t: TA[x] = E_hh + sum_{j<ta} s_j(x) F_j, TB[y] = sum s_j(y) F_{ta+j}
+            const int a = p.g, ta = p.ta, tb = a - ta;
+            const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
+            T *tb_s = tab + s * kTab;
+            for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
+                if (x < (1 << ta)) {
+                    T v = F[a];
+                    for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
+                    tb_s[x] = v;
+                } else {
+                    const int y = x - (1 << ta);
+                    T v = (T)0;
+                    for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
+                    tb_s[64 + y] = v;
+                }
+            }
+            __syncwarp();
+        }
         if (lane == 0) {
-            const long long first = n > kStages ? n - kStages : 0;
-            for (long long k = first; k < n; ++k)
-                mbar_wait(&full[(int)(k % kStages)], (unsigned)((k / kStages) & 1), p.err);
+            int crd[5];
+            coords(t, crd);
+            mbar_arrive_expect_tx(&full[s], p.tile_bytes);
+            tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &full[s]);
+            if (has_stream) tma_prefetch_l2(&tm_s, p.rank, crd);
         }
-        return;
+        return true;
+    };
+    long long issued = 0;  // tiles whose copies warp 0 has issued
+    if (warp == 0) {
+        for (long long t = blockIdx.x; t < p.ntiles && issued < kStages; t += gridDim.x) {
+            fill(issued, t);
+            ++issued;
+        }
     }
 
-    // ------------------------------ consumers ------------------------------
     const int tid = threadIdx.x;
     double sv = 1.0, ea = 0.0, eb = 0.0;
     if (p.epi != nullptr) {
@@ -299,66 +299,116 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
 
     double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
     long long n = 0;
+    bool failed = false;
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++n) {
         const int s = (int)(n % kStages);
         const unsigned ph = (unsigned)((n / kStages) & 1);
+        if (warp == 0 && n >= 1) {
+            // refill the stage released by tile n-1 with tile n-1+kStages
+            const long long tf = blockIdx.x + (n - 1 + kStages) * (long long)gridDim.x;
+            if (issued == n - 1 + kStages && tf < p.ntiles) {
+                if (!fill(issued, tf)) {
+                    if (lane == 0) atomicExch(p.err, 1);
+                    failed = true;
+                    break;
+                }
+                ++issued;
+            }
+        }
         const V *Ucur = U + (size_t)s * kTileV;
         const T *tcur = tab + s * kTab;
         const uint64_t tt = (uint64_t)t;
         const uint64_t base = ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
         if (!mbar_wait(&full[s], ph, p.err)) {
             atomicExch(p.err, 1);
+            failed = true;
             break;
         }
         T pd0 = 0, pd1 = 0, pn = 0;
+        const bool full_tile = (nmine == kBV);
         // two halves of four vectors keep the live registers low
-        C self[2][kHB * VE], r[2][kHB * VE];
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
+            C self[kHB * VE], r[kHB * VE], st[kHB * VE];
+            // elementwise stream first: its latency overlaps the flips
+            if (has_stream) {
+#pragma unroll
+                for (int i = 0; i < kHB; ++i) {
+                    const int ii = hh * kHB + i;
+                    if (full_tile || ii < nmine) unpack(__ldcs(&p.stream[gidx(base, ii * kPassThreads + tid)]), &st[i * VE]);
+                    else unpack(V{}, &st[i * VE]);
+                }
+            }
 #pragma unroll
             for (int i = 0; i < kHB; ++i) {
                 const int ii = hh * kHB + i;
-                if (ii < nmine) unpack(Ucur[ii * kPassThreads + tid], &self[hh][i * VE]);
-                else unpack(V{}, &self[hh][i * VE]);
+                if (full_tile || ii < nmine) unpack(Ucur[ii * kPassThreads + tid], &self[i * VE]);
+                else unpack(V{}, &self[i * VE]);
             }
 #pragma unroll
-            for (int e = 0; e < kHB * VE; ++e) r[hh][e] = C{(T)0, (T)0};
+            for (int e = 0; e < kHB * VE; ++e) r[e] = C{(T)0, (T)0};
             int k0 = 0;
             if (VE == 2 && p.c == 0) {
                 // bit 0 lives inside the 16-byte vector
                 const T f = p.hb[p.o];
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
-                    cfma(f, self[hh][i * VE + VE - 1], r[hh][i * VE]);
-                    cfma(f, self[hh][i * VE], r[hh][i * VE + VE - 1]);
+                    cfma(f, self[i * VE + VE - 1], r[i * VE]);
+                    cfma(f, self[i * VE], r[i * VE + VE - 1]);
                 }
                 k0 = 1;
             }
-            for (int k = k0; k < p.g; ++k) {
-                const T f = p.hb[p.o + k];
-                const int flip = 1 << (p.c + k - LOGVE);
+            if (full_tile) {
+                for (int k = k0; k < p.g; ++k) {
+                    const T f = p.hb[p.o + k];
+                    const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
-                for (int i = 0; i < kHB; ++i) {
-                    const int ii = hh * kHB + i;
-                    if (ii < nmine) {
+                    for (int i = 0; i < kHB; ++i) {
                         C x[VE];
-                        unpack(Ucur[(ii * kPassThreads + tid) ^ flip], x);
+                        unpack(Ucur[((hh * kHB + i) * kPassThreads + tid) ^ flip], x);
 #pragma unroll
-                        for (int e = 0; e < VE; ++e) cfma(f, x[e], r[hh][i * VE + e]);
+                        for (int e = 0; e < VE; ++e) cfma(f, x[e], r[i * VE + e]);
+                    }
+                }
+            } else {
+                for (int k = k0; k < p.g; ++k) {
+                    const T f = p.hb[p.o + k];
+                    const int flip = 1 << (p.c + k - LOGVE);
+#pragma unroll
+                    for (int i = 0; i < kHB; ++i) {
+                        const int ii = hh * kHB + i;
+                        if (ii < nmine) {
+                            C x[VE];
+                            unpack(Ucur[(ii * kPassThreads + tid) ^ flip], x);
+#pragma unroll
+                            for (int e = 0; e < VE; ++e) cfma(f, x[e], r[i * VE + e]);
+                        }
                     }
                 }
             }
             if (p.first) {
+                // E(b) - a for the VE amplitudes of each vector: contiguous table
+                // entries are read as one 8- or 16-byte load (no bank conflicts)
                 const int tmask = (1 << p.ta) - 1;
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
                     const int ii = hh * kHB + i;
-                    if (ii < nmine) {
+                    if (full_tile || ii < nmine) {
+                        const int li = (ii * kPassThreads + tid) << LOGVE;
+                        if (VE == 2 && p.ta >= 1) {
+                            const float2 el = __ldg(reinterpret_cast<const float2 *>(p.Ell) + (li >> 1));
+                            const float2 ta2 = reinterpret_cast<const float2 *>(tcur)[(li & tmask) >> 1];
+                            const float tbv = (float)tcur[64 + (li >> p.ta)] - (float)aT;
+                            const float E0 = el.x + ta2.x + tbv, E1 = el.y + ta2.y + tbv;
+                            cfma((T)E0, self[i * VE], r[i * VE]);
+                            cfma((T)E1, self[i * VE + VE - 1], r[i * VE + VE - 1]);
+                        } else {
 #pragma unroll
-                        for (int e = 0; e < VE; ++e) {
-                            const int li = ((ii * kPassThreads + tid) << LOGVE) + e;
-                            const T E = __ldg(&p.Ell[li]) + tcur[li & tmask] + tcur[64 + (li >> p.ta)] - aT;
-                            cfma(E, self[hh][i * VE + e], r[hh][i * VE + e]);
+                            for (int e = 0; e < VE; ++e) {
+                                const int le = li + e;
+                                const T E = __ldg(&p.Ell[le]) + tcur[le & tmask] + tcur[64 + (le >> p.ta)] - aT;
+                                cfma(E, self[i * VE + e], r[i * VE + e]);
+                            }
                         }
                     }
                 }
@@ -370,26 +420,18 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             }
             if (has_stream) {
 #pragma unroll
-                for (int i = 0; i < kHB; ++i) {
-                    const int ii = hh * kHB + i;
-                    if (ii < nmine) {
-                        C x[VE];
-                        unpack(__ldcs(&p.stream[gidx(base, ii * kPassThreads + tid)]), x);
-#pragma unroll
-                        for (int e = 0; e < VE; ++e) cfma(bsT, x[e], r[hh][i * VE + e]);
-                    }
-                }
+                for (int e = 0; e < kHB * VE; ++e) cfma(bsT, st[e], r[e]);
             }
             if (!p.last) {
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
                     const int ii = hh * kHB + i;
-                    if (ii < nmine) p.out[gidx(base, ii * kPassThreads + tid)] = pack(&r[hh][i * VE]);
+                    if (full_tile || ii < nmine) p.out[gidx(base, ii * kPassThreads + tid)] = pack(&r[i * VE]);
                 }
             } else if (p.epilogue == EPI_ENERGY) {
 #pragma unroll
                 for (int e = 0; e < kHB * VE; ++e) {
-                    const C &u = self[hh][e], &w = r[hh][e];
+                    const C &u = self[e], &w = r[e];
                     pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
                     pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
                     pn = fma(u.x, u.x, fma(u.y, u.y, pn));
@@ -397,18 +439,18 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             } else {
 #pragma unroll
                 for (int e = 0; e < kHB * VE; ++e) {
-                    r[hh][e].x *= svT;
-                    r[hh][e].y *= svT;
+                    r[e].x *= svT;
+                    r[e].y *= svT;
                 }
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
                     const int ii = hh * kHB + i;
-                    if (ii < nmine) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], pack(&r[hh][i * VE]));
+                    if (full_tile || ii < nmine) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], pack(&r[i * VE]));
                 }
                 if (p.epilogue == EPI_KRYLOV) {
 #pragma unroll
                     for (int e = 0; e < kHB * VE; ++e) {
-                        const C &u = self[hh][e], &w = r[hh][e];
+                        const C &u = self[e], &w = r[e];
                         pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
                         pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
                         pn = fma(w.x, w.x, fma(w.y, w.y, pn));
@@ -421,6 +463,12 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         acc_n += (double)pn;
     }
 
+    if (failed && warp == 0 && lane == 0) {
+        // every copy this CTA issued lands before it exits (bounded)
+        const long long first = issued > kStages ? issued - kStages : 0;
+        for (long long k = first; k < issued; ++k)
+            mbar_wait(&full[(int)(k % kStages)], (unsigned)((k / kStages) & 1), p.err);
+    }
     if (p.last && p.epilogue != EPI_PLAIN && p.partials != nullptr) {
         // per-warp partials (fixed order, no CTA barrier so early exits cannot hang)
 #pragma unroll
