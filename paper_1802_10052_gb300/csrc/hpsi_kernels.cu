@@ -297,6 +297,14 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         return (base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask)) >> LOGVE;
     };
 
+    // E_ll of this thread's amplitudes: they sit at the same low bits in every
+    // tile of the first pass, so the table is read once per launch
+    T ell[kBV * VE];
+#pragma unroll
+    for (int e = 0; e < kBV * VE; ++e) {
+        const int li = (((e / VE) * kPassThreads + tid) << LOGVE) + (e % VE);
+        ell[e] = (p.first && li < (nvec << LOGVE)) ? __ldg(&p.Ell[li]) : (T)0;
+    }
     double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
     long long n = 0;
     bool failed = false;
@@ -326,6 +334,13 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         }
         T pd0 = 0, pd1 = 0, pn = 0;
         const bool full_tile = (nmine == kBV);
+        // TA entries of this thread: the low ta bits of its amplitudes do not
+        // depend on the vector index i (512 << LOGVE >= 2^ta)
+        T ta_e[VE];
+        if (p.first) {
+#pragma unroll
+            for (int e = 0; e < VE; ++e) ta_e[e] = tcur[((tid << LOGVE) + e) & ((1 << p.ta) - 1)];
+        }
         // two halves of four vectors keep the live registers low
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
@@ -359,13 +374,37 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 k0 = 1;
             }
             if (full_tile) {
-                for (int k = k0; k < p.g; ++k) {
+                const int qb = hh * kHB * kPassThreads + tid;
+                int k = k0;
+                for (; k + 1 < p.g; k += 2) {
+                    // two flips per iteration: eight shared loads in flight
+                    const T f0 = p.hb[p.o + k], f1 = p.hb[p.o + k + 1];
+                    const int fl0 = 1 << (p.c + k - LOGVE), fl1 = fl0 << 1;
+                    V v0[kHB], v1[kHB];
+#pragma unroll
+                    for (int i = 0; i < kHB; ++i) {
+                        v0[i] = Ucur[(qb + i * kPassThreads) ^ fl0];
+                        v1[i] = Ucur[(qb + i * kPassThreads) ^ fl1];
+                    }
+#pragma unroll
+                    for (int i = 0; i < kHB; ++i) {
+                        C x[VE], y[VE];
+                        unpack(v0[i], x);
+                        unpack(v1[i], y);
+#pragma unroll
+                        for (int e = 0; e < VE; ++e) {
+                            cfma(f0, x[e], r[i * VE + e]);
+                            cfma(f1, y[e], r[i * VE + e]);
+                        }
+                    }
+                }
+                if (k < p.g) {
                     const T f = p.hb[p.o + k];
                     const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
                     for (int i = 0; i < kHB; ++i) {
                         C x[VE];
-                        unpack(Ucur[((hh * kHB + i) * kPassThreads + tid) ^ flip], x);
+                        unpack(Ucur[(qb + i * kPassThreads) ^ flip], x);
 #pragma unroll
                         for (int e = 0; e < VE; ++e) cfma(f, x[e], r[i * VE + e]);
                     }
@@ -387,28 +426,18 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
             if (p.first) {
-                // E(b) - a for the VE amplitudes of each vector: contiguous table
-                // entries are read as one 8- or 16-byte load (no bank conflicts)
-                const int tmask = (1 << p.ta) - 1;
+                // E(b) - a = E_ll (registers) + TA (low ta bits, fixed per thread)
+                //           + TB (bits above ta) - a
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
                     const int ii = hh * kHB + i;
                     if (full_tile || ii < nmine) {
                         const int li = (ii * kPassThreads + tid) << LOGVE;
-                        if (VE == 2 && p.ta >= 1) {
-                            const float2 el = __ldg(reinterpret_cast<const float2 *>(p.Ell) + (li >> 1));
-                            const float2 ta2 = reinterpret_cast<const float2 *>(tcur)[(li & tmask) >> 1];
-                            const float tbv = (float)tcur[64 + (li >> p.ta)] - (float)aT;
-                            const float E0 = el.x + ta2.x + tbv, E1 = el.y + ta2.y + tbv;
-                            cfma((T)E0, self[i * VE], r[i * VE]);
-                            cfma((T)E1, self[i * VE + VE - 1], r[i * VE + VE - 1]);
-                        } else {
+                        const T tbv = tcur[64 + (li >> p.ta)] - aT;
 #pragma unroll
-                            for (int e = 0; e < VE; ++e) {
-                                const int le = li + e;
-                                const T E = __ldg(&p.Ell[le]) + tcur[le & tmask] + tcur[64 + (le >> p.ta)] - aT;
-                                cfma(E, self[i * VE + e], r[i * VE + e]);
-                            }
+                        for (int e = 0; e < VE; ++e) {
+                            const T E = ell[ii * VE + e] + ta_e[e] + tbv;
+                            cfma(E, self[i * VE + e], r[i * VE + e]);
                         }
                     }
                 }
