@@ -183,6 +183,32 @@ osmps_status osmps_ed_measure_corr(osmps_ed_t *ed, const void *psi, double *szsz
 osmps_status osmps_ed_measure_zz(osmps_ed_t *ed, const void *psi, double *sz, double *szsz);
 
 /*
+ * <sz_k> and <sz_i sz_j> like osmps_ed_measure_zz, but without a handle and
+ * without allocating any memory.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory at run time,
+ * e.g. code whose device memory is owned by another allocator or budget (a
+ * framework's caching pool), or a latency-critical loop that cannot afford
+ * cudaMalloc/cudaFree and the device-wide synchronisation they imply.
+ *   L         1 <= L <= OSMPS_MAX_L (30); larger chains return OSMPS_EINVAL.
+ *   prec      OSMPS_FP64 (psi is complex128) or OSMPS_MIXED (complex64).
+ *   psi       device state, 2^L elements, 16-byte aligned.
+ *   out_dev   device array of L + L*L doubles: <sz_k> for k = 1..L, then
+ *             <sz_i sz_j> row-major (site order, diagonal = <psi|psi>).
+ *   cuda_stream  stream the kernels are enqueued on; the call does not
+ *             synchronise.
+ * Scratch: a file-scope device array of 3.75 MiB (3,932,160 bytes) that every
+ * GPU loading this library holds until the process exits.  All calls share it
+ * and it keeps the last call's contents; every entry a call reads was written
+ * earlier in the same call, so nothing needs clearing.  Calls that overlap on
+ * the GPU (different streams, or different host threads) race on the scratch:
+ * order them.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ */
+osmps_status osmps_ed_measure_zz_noalloc(int L, int prec, const void *psi, double *out_dev, void *cuda_stream);
+
+/*
  * Schmidt spectrum and entanglement entropy of the bipartition sites 1..cut |
  * cut+1..L (Sec. IV, bond entropy: rho = M M^dagger with M the state reshaped
  * to (2^cut, 2^(L-cut)); S = -sum_j Lambda_j ln Lambda_j, Sec. V).

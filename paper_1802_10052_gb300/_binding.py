@@ -41,6 +41,7 @@ SIGNATURES = {
     "osmps_ed_measure_local": (_I, [_P, _P, _DP]),
     "osmps_ed_measure_corr": (_I, [_P, _P, _DP]),
     "osmps_ed_measure_zz": (_I, [_P, _P, _DP, _DP]),
+    "osmps_ed_measure_zz_noalloc": (_I, [_I, _I, _P, _P, _P]),
     "osmps_ed_schmidt_entropy": (_I, [_P, _P, _I, _DP, _DP]),
     "osmps_ed_launch_count": (_I, [_P, C.POINTER(C.c_int64)]),
     "osmps_ed_timing_enable": (_I, [_P, _I]),

@@ -14,6 +14,8 @@
 #include <dlfcn.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "ed_internal.h"
 
 namespace osmps {
@@ -213,6 +215,80 @@ static cudaError_t zstats_t(Handle *h, const void *psi, double *out_dev) {
 cudaError_t launch_zstats(Handle *h, const void *psi, double *out_dev) {
     return h->prec == OSMPS_FP64 ? zstats_t<double>(h, psi, out_dev) : zstats_t<float>(h, psi, out_dev);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the measurement pass.
+//
+// Its per-CTA partial sums live in one file-scope device array instead of
+// handle-owned memory.  Every GPU that loads this library holds the array
+// (kNoAllocScratch doubles, 3.75 MiB) until the process exits.  Host code must
+// not pass the array's name to a kernel (on the host it is only a stand-in
+// symbol); the device address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocGrid = 96;  // CTAs of the measurement pass
+constexpr size_t kNoAllocScratch = 491520;  // >= 96 * (931 + 4096) + 931 + 4096 for L <= 30
+static_assert((size_t)kNoAllocGrid * (30 * 30 + 30 + 1 + (1u << kZTileBits)) + 30 * 30 + 30 + 1 +
+                      (1u << kZTileBits) <=
+                  kNoAllocScratch,
+              "scratch too small for L = 30");
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+static std::mutex g_noalloc_mutex;
+static double *g_noalloc_ptr[128];  // device address of g_noalloc_scratch per device ordinal
+
+template <typename T>
+static cudaError_t zstats_noalloc_t(int L, const void *psi, double *out_dev, double *scratch, cudaStream_t st) {
+    const int t = L < kZTileBits ? L : kZTileBits;
+    const long long ntiles = 1ll << (L - t);
+    const int grid = (int)(ntiles < kNoAllocGrid ? ntiles : kNoAllocGrid);
+    const int nacc = zacc_count(L), nel = 1 << t;
+    double *blockacc = scratch;
+    double *Gpart = scratch + (size_t)grid * nacc;
+    double *red = Gpart + (size_t)grid * nel;
+    zstats_kernel<T><<<grid, kZThreads, 0, st>>>(reinterpret_cast<const typename ZV<T>::c *>(psi), L, t, ntiles,
+                                                  blockacc, Gpart);
+    const int nw1 = nacc + nel;
+    zstats_reduce_kernel<<<(nw1 + 7) / 8, 256, 0, st>>>(blockacc, Gpart, grid, nacc, nel, red);
+    const int nw2 = L + L * L;
+    zstats_assemble_kernel<<<(nw2 + 7) / 8, 256, 0, st>>>(red, L, t, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace osmps
+
+extern "C" osmps_status osmps_ed_measure_zz_noalloc(int L, int prec, const void *psi, double *out_dev,
+                                                    void *cuda_stream) {
+    using namespace osmps;
+    if (L < 1 || L > OSMPS_MAX_L) return OSMPS_EINVAL;
+    if (prec != OSMPS_FP64 && prec != OSMPS_MIXED) return OSMPS_EINVAL;
+    if (psi == nullptr || out_dev == nullptr || ((uintptr_t)psi & 15u) != 0 || ((uintptr_t)out_dev & 7u) != 0)
+        return OSMPS_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+        cudaGetLastError();
+        return OSMPS_ECUDA;
+    }
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (g_noalloc_ptr[dev] == nullptr) {
+            void *addr = nullptr;
+            if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || addr == nullptr) {
+                cudaGetLastError();
+                return OSMPS_ECUDA;
+            }
+            g_noalloc_ptr[dev] = (double *)addr;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    cudaError_t err = (prec == OSMPS_FP64)
+                          ? zstats_noalloc_t<double>(L, psi, out_dev, scratch, (cudaStream_t)cuda_stream)
+                          : zstats_noalloc_t<float>(L, psi, out_dev, scratch, (cudaStream_t)cuda_stream);
+    return err == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
+}
+
+namespace osmps {
 
 // ---------------------------------------------------------------------------
 // Gram product rho[x][y] = sum_k A[x,k] conj(A[y,k]),  A[x,k] = psi[x*sx + k*sk]
