@@ -33,19 +33,22 @@
 namespace osmps {
 
 template <typename T> struct Cx;
+// complex64: an amplitude is one 64-bit register pair {re, im} used directly by
+// the packed FP32x2 instructions; a 16-byte vector holds two amplitudes.
 template <> struct Cx<float> {
-    typedef float2 c;
-    typedef float4 v16;
-    static constexpr int VE = 2;     // amplitudes per 16-byte vector
+    typedef ulonglong2 v16;
+    typedef unsigned long long amp;
+    typedef unsigned long long coef;   // {f, f}
+    static constexpr int VE = 2;       // amplitudes per 16-byte vector
     static constexpr int LOGVE = 1;
-    static constexpr int BLOG = 4;   // log2 amplitudes per register block (8 vectors)
 };
+// complex128: one amplitude per 16-byte vector, FP64 arithmetic
 template <> struct Cx<double> {
-    typedef double2 c;
     typedef double2 v16;
+    typedef double2 amp;
+    typedef double coef;
     static constexpr int VE = 1;
     static constexpr int LOGVE = 0;
-    static constexpr int BLOG = 3;
 };
 
 constexpr int kBV = 8;                                  // 16-byte vectors per consumer thread per tile
@@ -75,33 +78,45 @@ struct PassParams {
     T hb[kMaxL + 1];
 };
 
-__device__ __forceinline__ void unpack(const float4 &v, float2 *e) {
-    e[0] = make_float2(v.x, v.y);
-    e[1] = make_float2(v.z, v.w);
+__device__ __forceinline__ void unpackv(const ulonglong2 &v, unsigned long long *a) {
+    a[0] = v.x;
+    a[1] = v.y;
 }
-__device__ __forceinline__ float4 pack(const float2 *e) { return make_float4(e[0].x, e[0].y, e[1].x, e[1].y); }
-__device__ __forceinline__ void unpack(const double2 &v, double2 *e) { e[0] = v; }
-__device__ __forceinline__ double2 pack(const double2 *e) { return e[0]; }
+__device__ __forceinline__ ulonglong2 packv(const unsigned long long *a) { return make_ulonglong2(a[0], a[1]); }
+__device__ __forceinline__ void unpackv(const double2 &v, double2 *a) { a[0] = v; }
+__device__ __forceinline__ double2 packv(const double2 *a) { return a[0]; }
 
-// acc += f * x on a complex amplitude: one packed FP32x2 FMA (operands are
-// register pairs), or two FP64 FMAs
-__device__ __forceinline__ void cfma(float f, const float2 &x, float2 &acc) {
-    asm("{\n .reg .b64 a, m, v;\n mov.b64 a, {%0, %1};\n mov.b64 m, {%2, %2};\n mov.b64 v, {%3, %4};\n"
-        " fma.rn.f32x2 a, m, v, a;\n mov.b64 {%0, %1}, a;\n}\n"
-        : "+f"(acc.x), "+f"(acc.y)
-        : "f"(f), "f"(x.x), "f"(x.y));
+__device__ __forceinline__ unsigned long long mkcoef(float f) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(f));
+    return r;
 }
-__device__ __forceinline__ void cfma(double f, const double2 &x, double2 &acc) {
+__device__ __forceinline__ double mkcoef(double f) { return f; }
+__device__ __forceinline__ unsigned long long azero(float) { return 0ull; }
+__device__ __forceinline__ double2 azero(double) { return make_double2(0.0, 0.0); }
+
+// acc += f * x on complex amplitudes (f real): one fma.rn.f32x2, or two FP64 FMAs
+__device__ __forceinline__ void afma(unsigned long long f, unsigned long long x, unsigned long long &acc) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(f), "l"(x));
+}
+__device__ __forceinline__ void afma(double f, const double2 &x, double2 &acc) {
     acc.x = fma(f, x.x, acc.x);
     acc.y = fma(f, x.y, acc.y);
 }
-// acc += (f0, f1) * x elementwise on a pair of reals
-__device__ __forceinline__ void cfma2(float f0, float f1, const float2 &x, float2 &acc) {
-    asm("{\n .reg .b64 a, m, v;\n mov.b64 a, {%0, %1};\n mov.b64 m, {%2, %3};\n mov.b64 v, {%4, %5};\n"
-        " fma.rn.f32x2 a, m, v, a;\n mov.b64 {%0, %1}, a;\n}\n"
-        : "+f"(acc.x), "+f"(acc.y)
-        : "f"(f0), "f"(f1), "f"(x.x), "f"(x.y));
+// a *= f
+__device__ __forceinline__ void amul(unsigned long long f, unsigned long long &a) {
+    asm("mul.rn.f32x2 %0, %1, %0;" : "+l"(a) : "l"(f));
 }
+__device__ __forceinline__ void amul(double f, double2 &a) {
+    a.x *= f;
+    a.y *= f;
+}
+__device__ __forceinline__ float2 tocx(unsigned long long a) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+    return r;
+}
+__device__ __forceinline__ double2 tocx(const double2 &a) { return a; }
 
 // ---- mbarrier / TMA primitives (PTX) ----
 __device__ __forceinline__ unsigned smem_u32(const void *ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
@@ -190,8 +205,9 @@ template <typename T>
 __global__ void __launch_bounds__(kHpsiThreads, 1)
     hpsi_pass_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
                      PassParams<T> p) {
-    typedef typename Cx<T>::c C;
     typedef typename Cx<T>::v16 V;
+    typedef typename Cx<T>::amp A;
+    typedef typename Cx<T>::coef K;
     constexpr int VE = Cx<T>::VE;
     constexpr int LOGVE = Cx<T>::LOGVE;
 
@@ -344,32 +360,32 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         // two halves of four vectors keep the live registers low
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-            C self[kHB * VE], r[kHB * VE], st[kHB * VE];
+            A self[kHB * VE], r[kHB * VE], st[kHB * VE];
             // elementwise stream first: its latency overlaps the flips
             if (has_stream) {
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
                     const int ii = hh * kHB + i;
-                    if (full_tile || ii < nmine) unpack(__ldcs(&p.stream[gidx(base, ii * kPassThreads + tid)]), &st[i * VE]);
-                    else unpack(V{}, &st[i * VE]);
+                    if (full_tile || ii < nmine) unpackv(__ldcs(&p.stream[gidx(base, ii * kPassThreads + tid)]), &st[i * VE]);
+                    else unpackv(V{}, &st[i * VE]);
                 }
             }
 #pragma unroll
             for (int i = 0; i < kHB; ++i) {
                 const int ii = hh * kHB + i;
-                if (full_tile || ii < nmine) unpack(Ucur[ii * kPassThreads + tid], &self[i * VE]);
-                else unpack(V{}, &self[i * VE]);
+                if (full_tile || ii < nmine) unpackv(Ucur[ii * kPassThreads + tid], &self[i * VE]);
+                else unpackv(V{}, &self[i * VE]);
             }
 #pragma unroll
-            for (int e = 0; e < kHB * VE; ++e) r[e] = C{(T)0, (T)0};
+            for (int e = 0; e < kHB * VE; ++e) r[e] = azero(T(0));
             int k0 = 0;
             if (VE == 2 && p.c == 0) {
                 // bit 0 lives inside the 16-byte vector
-                const T f = p.hb[p.o];
+                const K f = mkcoef(p.hb[p.o]);
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
-                    cfma(f, self[i * VE + VE - 1], r[i * VE]);
-                    cfma(f, self[i * VE], r[i * VE + VE - 1]);
+                    afma(f, self[i * VE + VE - 1], r[i * VE]);
+                    afma(f, self[i * VE], r[i * VE + VE - 1]);
                 }
                 k0 = 1;
             }
@@ -378,7 +394,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 int k = k0;
                 for (; k + 1 < p.g; k += 2) {
                     // two flips per iteration: eight shared loads in flight
-                    const T f0 = p.hb[p.o + k], f1 = p.hb[p.o + k + 1];
+                    const K f0 = mkcoef(p.hb[p.o + k]), f1 = mkcoef(p.hb[p.o + k + 1]);
                     const int fl0 = 1 << (p.c + k - LOGVE), fl1 = fl0 << 1;
                     V v0[kHB], v1[kHB];
 #pragma unroll
@@ -388,39 +404,39 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                     }
 #pragma unroll
                     for (int i = 0; i < kHB; ++i) {
-                        C x[VE], y[VE];
-                        unpack(v0[i], x);
-                        unpack(v1[i], y);
+                        A x[VE], y[VE];
+                        unpackv(v0[i], x);
+                        unpackv(v1[i], y);
 #pragma unroll
                         for (int e = 0; e < VE; ++e) {
-                            cfma(f0, x[e], r[i * VE + e]);
-                            cfma(f1, y[e], r[i * VE + e]);
+                            afma(f0, x[e], r[i * VE + e]);
+                            afma(f1, y[e], r[i * VE + e]);
                         }
                     }
                 }
                 if (k < p.g) {
-                    const T f = p.hb[p.o + k];
+                    const K f = mkcoef(p.hb[p.o + k]);
                     const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
                     for (int i = 0; i < kHB; ++i) {
-                        C x[VE];
-                        unpack(Ucur[(qb + i * kPassThreads) ^ flip], x);
+                        A x[VE];
+                        unpackv(Ucur[(qb + i * kPassThreads) ^ flip], x);
 #pragma unroll
-                        for (int e = 0; e < VE; ++e) cfma(f, x[e], r[i * VE + e]);
+                        for (int e = 0; e < VE; ++e) afma(f, x[e], r[i * VE + e]);
                     }
                 }
             } else {
                 for (int k = k0; k < p.g; ++k) {
-                    const T f = p.hb[p.o + k];
+                    const K f = mkcoef(p.hb[p.o + k]);
                     const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
                     for (int i = 0; i < kHB; ++i) {
                         const int ii = hh * kHB + i;
                         if (ii < nmine) {
-                            C x[VE];
-                            unpack(Ucur[(ii * kPassThreads + tid) ^ flip], x);
+                            A x[VE];
+                            unpackv(Ucur[(ii * kPassThreads + tid) ^ flip], x);
 #pragma unroll
-                            for (int e = 0; e < VE; ++e) cfma(f, x[e], r[i * VE + e]);
+                            for (int e = 0; e < VE; ++e) afma(f, x[e], r[i * VE + e]);
                         }
                     }
                 }
@@ -437,7 +453,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
 #pragma unroll
                         for (int e = 0; e < VE; ++e) {
                             const T E = ell[ii * VE + e] + ta_e[e] + tbv;
-                            cfma(E, self[i * VE + e], r[i * VE + e]);
+                            afma(mkcoef(E), self[i * VE + e], r[i * VE + e]);
                         }
                     }
                 }
@@ -448,38 +464,37 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
             if (has_stream) {
+                const K bsK = mkcoef(bsT);
 #pragma unroll
-                for (int e = 0; e < kHB * VE; ++e) cfma(bsT, st[e], r[e]);
+                for (int e = 0; e < kHB * VE; ++e) afma(bsK, st[e], r[e]);
             }
             if (!p.last) {
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
                     const int ii = hh * kHB + i;
-                    if (full_tile || ii < nmine) p.out[gidx(base, ii * kPassThreads + tid)] = pack(&r[i * VE]);
+                    if (full_tile || ii < nmine) p.out[gidx(base, ii * kPassThreads + tid)] = packv(&r[i * VE]);
                 }
             } else if (p.epilogue == EPI_ENERGY) {
 #pragma unroll
                 for (int e = 0; e < kHB * VE; ++e) {
-                    const C &u = self[e], &w = r[e];
+                    const auto u = tocx(self[e]), w = tocx(r[e]);
                     pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
                     pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
                     pn = fma(u.x, u.x, fma(u.y, u.y, pn));
                 }
             } else {
+                const K svK = mkcoef(svT);
 #pragma unroll
-                for (int e = 0; e < kHB * VE; ++e) {
-                    r[e].x *= svT;
-                    r[e].y *= svT;
-                }
+                for (int e = 0; e < kHB * VE; ++e) amul(svK, r[e]);
 #pragma unroll
                 for (int i = 0; i < kHB; ++i) {
                     const int ii = hh * kHB + i;
-                    if (full_tile || ii < nmine) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], pack(&r[i * VE]));
+                    if (full_tile || ii < nmine) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], packv(&r[i * VE]));
                 }
                 if (p.epilogue == EPI_KRYLOV) {
 #pragma unroll
                     for (int e = 0; e < kHB * VE; ++e) {
-                        const C &u = self[e], &w = r[e];
+                        const auto u = tocx(self[e]), w = tocx(r[e]);
                         pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
                         pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
                         pn = fma(w.x, w.x, fma(w.y, w.y, pn));
