@@ -144,15 +144,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait for the phase of the given parity; gives up after kWaitNs or when
-// another thread has already raised the error flag.
+// Wait for the phase of the given parity.  try_wait itself suspends the
+// thread for a while; the timer (and the error flag raised by another warp)
+// is consulted only every 64 polls, so a completed phase is seen at once.
+// Gives up after kWaitNs.
 __device__ __noinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, const int *err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (true) {
+    for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (*(volatile const int *)err != 0) return false;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if ((it & 63u) == 0) {
+            if (*(volatile const int *)err != 0) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
     }
 }
 __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *tm, int rank, const int *crd,
