@@ -308,7 +308,10 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     }
     // first pass: r = H_inner u - a u - (b/sv) uprev ;  last pass: w = sv * r
     const T aT = (T)ea;
-    const T bsT = (p.first && has_stream) ? (T)(-eb / sv) : (T)1;
+    // stream coefficient bs: -b/sv for the previous vector in the first pass, 1 for a partial sum
+    const double bs = (p.first && has_stream) ? -eb / sv : 1.0;
+    const bool use_stream = has_stream && bs != 0.0;
+    const T kap = use_stream ? (T)(1.0 / bs) : (T)1, ikap = use_stream ? (T)bs : (T)1;
     const T svT = (T)sv;
     const int nmine =
         tid < nvec ? ((nvec - 1 - tid) / kPassThreads + 1 < kBV ? (nvec - 1 - tid) / kPassThreads + 1 : kBV) : 0;
@@ -361,149 +364,121 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
 #pragma unroll
             for (int e = 0; e < VE; ++e) ta_e[e] = tcur[((tid << LOGVE) + e) & ((1 << p.ta) - 1)];
         }
-        // two halves of four vectors keep the live registers low
+        // The accumulators start from the elementwise stream (partial sum, or
+        // the previous Lanczos vector); flip and diagonal coefficients are
+        // scaled by kap = 1/bs so that r / kap is the wanted sum.
+        A self[kBV * VE], r[kBV * VE];
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            A self[kHB * VE], r[kHB * VE], st[kHB * VE];
-            // elementwise stream first: its latency overlaps the flips
-            if (has_stream) {
+        for (int i = 0; i < kBV; ++i) {
+            if (use_stream && (full_tile || i < nmine))
+                unpackv(__ldcs(&p.stream[gidx(base, i * kPassThreads + tid)]), &r[i * VE]);
+            else
+                unpackv(V{}, &r[i * VE]);
+        }
 #pragma unroll
-                for (int i = 0; i < kHB; ++i) {
-                    const int ii = hh * kHB + i;
-                    if (full_tile || ii < nmine) unpackv(__ldcs(&p.stream[gidx(base, ii * kPassThreads + tid)]), &st[i * VE]);
-                    else unpackv(V{}, &st[i * VE]);
-                }
+        for (int i = 0; i < kBV; ++i) {
+            if (full_tile || i < nmine) unpackv(Ucur[i * kPassThreads + tid], &self[i * VE]);
+            else unpackv(V{}, &self[i * VE]);
+        }
+        // flips of bits held in registers: the amplitude bit inside a vector
+        // (first pass) and the three bits of the vector index i
+        if (VE == 2 && p.c == 0) {
+            const K f = mkcoef(p.hb[p.o] * kap);
+#pragma unroll
+            for (int i = 0; i < kBV; ++i) {
+                afma(f, self[i * VE + VE - 1], r[i * VE]);
+                afma(f, self[i * VE], r[i * VE + VE - 1]);
             }
+        }
 #pragma unroll
-            for (int i = 0; i < kHB; ++i) {
-                const int ii = hh * kHB + i;
-                if (full_tile || ii < nmine) unpackv(Ucur[ii * kPassThreads + tid], &self[i * VE]);
-                else unpackv(V{}, &self[i * VE]);
+        for (int j = 0; j < 3; ++j) {
+            const int lb = LOGVE + 9 + j;  // local bit carried by bit j of i
+            if (lb >= p.c && lb < tbits) {
+                const K f = mkcoef(p.hb[p.o + lb - p.c] * kap);
+#pragma unroll
+                for (int i = 0; i < kBV; ++i)
+#pragma unroll
+                    for (int e = 0; e < VE; ++e) afma(f, self[(i ^ (1 << j)) * VE + e], r[i * VE + e]);
             }
+        }
+        // flips of bits across threads: neighbour vectors from shared memory
+        {
+            const int lb0 = p.c > LOGVE ? p.c : LOGVE;
+            const int lb1 = tbits < LOGVE + 9 ? tbits : LOGVE + 9;
+            for (int lb = lb0; lb < lb1; ++lb) {
+                const K f = mkcoef(p.hb[p.o + lb - p.c] * kap);
+                const int flip = 1 << (lb - LOGVE);
 #pragma unroll
-            for (int e = 0; e < kHB * VE; ++e) r[e] = azero(T(0));
-            int k0 = 0;
-            if (VE == 2 && p.c == 0) {
-                // bit 0 lives inside the 16-byte vector
-                const K f = mkcoef(p.hb[p.o]);
-#pragma unroll
-                for (int i = 0; i < kHB; ++i) {
-                    afma(f, self[i * VE + VE - 1], r[i * VE]);
-                    afma(f, self[i * VE], r[i * VE + VE - 1]);
-                }
-                k0 = 1;
-            }
-            if (full_tile) {
-                const int qb = hh * kHB * kPassThreads + tid;
-                int k = k0;
-                for (; k + 1 < p.g; k += 2) {
-                    // two flips per iteration: eight shared loads in flight
-                    const K f0 = mkcoef(p.hb[p.o + k]), f1 = mkcoef(p.hb[p.o + k + 1]);
-                    const int fl0 = 1 << (p.c + k - LOGVE), fl1 = fl0 << 1;
-                    V v0[kHB], v1[kHB];
+                for (int h4 = 0; h4 < 2; ++h4) {
+                    V v[kHB];
 #pragma unroll
                     for (int i = 0; i < kHB; ++i) {
-                        v0[i] = Ucur[(qb + i * kPassThreads) ^ fl0];
-                        v1[i] = Ucur[(qb + i * kPassThreads) ^ fl1];
+                        const int ii = h4 * kHB + i;
+                        if (full_tile || ii < nmine) v[i] = Ucur[(ii * kPassThreads + tid) ^ flip];
+                        else v[i] = V{};
                     }
-#pragma unroll
-                    for (int i = 0; i < kHB; ++i) {
-                        A x[VE], y[VE];
-                        unpackv(v0[i], x);
-                        unpackv(v1[i], y);
-#pragma unroll
-                        for (int e = 0; e < VE; ++e) {
-                            afma(f0, x[e], r[i * VE + e]);
-                            afma(f1, y[e], r[i * VE + e]);
-                        }
-                    }
-                }
-                if (k < p.g) {
-                    const K f = mkcoef(p.hb[p.o + k]);
-                    const int flip = 1 << (p.c + k - LOGVE);
 #pragma unroll
                     for (int i = 0; i < kHB; ++i) {
                         A x[VE];
-                        unpackv(Ucur[(qb + i * kPassThreads) ^ flip], x);
+                        unpackv(v[i], x);
 #pragma unroll
-                        for (int e = 0; e < VE; ++e) afma(f, x[e], r[i * VE + e]);
-                    }
-                }
-            } else {
-                for (int k = k0; k < p.g; ++k) {
-                    const K f = mkcoef(p.hb[p.o + k]);
-                    const int flip = 1 << (p.c + k - LOGVE);
-#pragma unroll
-                    for (int i = 0; i < kHB; ++i) {
-                        const int ii = hh * kHB + i;
-                        if (ii < nmine) {
-                            A x[VE];
-                            unpackv(Ucur[(ii * kPassThreads + tid) ^ flip], x);
-#pragma unroll
-                            for (int e = 0; e < VE; ++e) afma(f, x[e], r[i * VE + e]);
-                        }
+                        for (int e = 0; e < VE; ++e) afma(f, x[e], r[(h4 * kHB + i) * VE + e]);
                     }
                 }
             }
-            if (p.first) {
-                // E(b) - a = E_ll (registers) + TA (low ta bits, fixed per thread)
-                //           + TB (bits above ta) - a
+        }
+        if (p.first) {
+            // (E(b) - a) kap = (E_ll + TA + TB - a) kap
 #pragma unroll
-                for (int i = 0; i < kHB; ++i) {
-                    const int ii = hh * kHB + i;
-                    if (full_tile || ii < nmine) {
-                        const int li = (ii * kPassThreads + tid) << LOGVE;
-                        const T tbv = tcur[64 + (li >> p.ta)] - aT;
+            for (int i = 0; i < kBV; ++i) {
+                if (full_tile || i < nmine) {
+                    const int li = (i * kPassThreads + tid) << LOGVE;
+                    const T tbv = tcur[64 + (li >> p.ta)] - aT;
 #pragma unroll
-                        for (int e = 0; e < VE; ++e) {
-                            const T E = ell[ii * VE + e] + ta_e[e] + tbv;
-                            afma(mkcoef(E), self[i * VE + e], r[i * VE + e]);
-                        }
+                    for (int e = 0; e < VE; ++e) {
+                        const T E = (ell[i * VE + e] + ta_e[e] + tbv) * kap;
+                        afma(mkcoef(E), self[i * VE + e], r[i * VE + e]);
                     }
                 }
             }
-            if (hh == 1) {
-                // stage s is no longer read by this warp
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);
+        }
+        // stage s is no longer read by this warp
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+
+        // r <- r / kap (and * sv in the last pass)
+        {
+            const T sc = (p.last && p.epilogue != EPI_ENERGY) ? ikap * svT : ikap;
+            if (sc != (T)1) {
+                const K scK = mkcoef(sc);
+#pragma unroll
+                for (int e = 0; e < kBV * VE; ++e) amul(scK, r[e]);
             }
-            if (has_stream) {
-                const K bsK = mkcoef(bsT);
+        }
+        if (!p.last || p.epilogue == EPI_PLAIN || p.epilogue == EPI_KRYLOV) {
 #pragma unroll
-                for (int e = 0; e < kHB * VE; ++e) afma(bsK, st[e], r[e]);
+            for (int i = 0; i < kBV; ++i) {
+                if (full_tile || i < nmine) {
+                    if (p.last) st_stream(&p.out[gidx(base, i * kPassThreads + tid)], packv(&r[i * VE]));
+                    else p.out[gidx(base, i * kPassThreads + tid)] = packv(&r[i * VE]);
+                }
             }
-            if (!p.last) {
+        }
+        if (p.last && p.epilogue == EPI_ENERGY) {
 #pragma unroll
-                for (int i = 0; i < kHB; ++i) {
-                    const int ii = hh * kHB + i;
-                    if (full_tile || ii < nmine) p.out[gidx(base, ii * kPassThreads + tid)] = packv(&r[i * VE]);
-                }
-            } else if (p.epilogue == EPI_ENERGY) {
+            for (int e = 0; e < kBV * VE; ++e) {
+                const auto u = tocx(self[e]), w = tocx(r[e]);
+                pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
+                pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
+                pn = fma(u.x, u.x, fma(u.y, u.y, pn));
+            }
+        } else if (p.last && p.epilogue == EPI_KRYLOV) {
 #pragma unroll
-                for (int e = 0; e < kHB * VE; ++e) {
-                    const auto u = tocx(self[e]), w = tocx(r[e]);
-                    pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
-                    pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
-                    pn = fma(u.x, u.x, fma(u.y, u.y, pn));
-                }
-            } else {
-                const K svK = mkcoef(svT);
-#pragma unroll
-                for (int e = 0; e < kHB * VE; ++e) amul(svK, r[e]);
-#pragma unroll
-                for (int i = 0; i < kHB; ++i) {
-                    const int ii = hh * kHB + i;
-                    if (full_tile || ii < nmine) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], packv(&r[i * VE]));
-                }
-                if (p.epilogue == EPI_KRYLOV) {
-#pragma unroll
-                    for (int e = 0; e < kHB * VE; ++e) {
-                        const auto u = tocx(self[e]), w = tocx(r[e]);
-                        pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
-                        pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
-                        pn = fma(w.x, w.x, fma(w.y, w.y, pn));
-                    }
-                }
+            for (int e = 0; e < kBV * VE; ++e) {
+                const auto u = tocx(self[e]), w = tocx(r[e]);
+                pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
+                pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
+                pn = fma(w.x, w.x, fma(w.y, w.y, pn));
             }
         }
         acc_d0 += (double)pd0;
