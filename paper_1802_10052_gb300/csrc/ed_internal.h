@@ -15,7 +15,7 @@ namespace osmps {
 constexpr int kMaxL = OSMPS_MAX_L;
 constexpr int kMaxKrylov = 64;       // vectors per Krylov step
 constexpr int kMaxLanczos = 1000;    // Lanczos vectors
-constexpr int kPassThreads = 512;    // threads per CTA of the H.psi passes
+constexpr int kPassThreads = 256;    // consumer threads per CTA of the H.psi passes
 constexpr int kVecThreads = 256;     // threads per CTA of the streaming vector kernels
 constexpr int kTileBytesLog2 = 16;   // 64 KiB shared-memory tile per H.psi CTA
 constexpr int kChunkBytesLog2 = 7;   // 128-byte contiguous chunks in the strided passes

@@ -51,15 +51,18 @@ template <> struct Cx<double> {
     static constexpr int LOGVE = 0;
 };
 
-constexpr int kBV = 8;                                  // 16-byte vectors per consumer thread per tile
+constexpr int kBV = 16;                                 // 16-byte vectors per consumer thread per tile
 constexpr int kHB = kBV / 2;                            // processed in two halves
 constexpr int kTileV = 1 << (kTileBytesLog2 - 4);       // 16-byte vectors per tile
 constexpr int kTab = 256;                               // TA (<= 64) + TB (<= 128) per stage
-constexpr int kStages = 3;                              // shared-memory ring of tiles
-constexpr int kConsumerWarps = kPassThreads / 32;       // 16
-constexpr int kHpsiThreads = kPassThreads;              // warp 0 also issues the copies
+constexpr int kStages = 2;                              // shared-memory ring of u tiles
+constexpr int kConsumerWarps = kPassThreads / 32;       // 8
+constexpr int kIBits = 4;                               // log2 kBV: vector-index bits held in registers
+constexpr int kTBits = 8;                               // log2 kPassThreads
+constexpr int kHpsiThreads = kPassThreads + 32;         // + one producer warp
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
-static_assert(kTileV == kBV * kPassThreads, "eight vectors per consumer thread per tile");
+static_assert(kTileV == kBV * kPassThreads && (1 << kIBits) == kBV && (1 << kTBits) == kPassThreads,
+              "sixteen vectors per consumer thread per tile");
 
 template <typename T>
 struct PassParams {
@@ -195,16 +198,18 @@ __device__ __forceinline__ void st_stream(V *ptr, const V &v) {
 }
 
 // One pass of the product, warp-specialized and persistent (one CTA per SM):
-//  * a 3-stage shared-memory ring holds tiles of u, filled by TMA
-//    (cp.async.bulk.tensor, completion on the stage's "full" mbarrier); warp 0
-//    refills a stage as soon as all 16 warps have released it on its "empty"
-//    mbarrier, prefetches the matching tile of the elementwise stream into L2
-//    and, in the first pass, builds the tile's diagonal tables;
-//  * every warp waits on "full", forms the flips, diagonal, stream term and
-//    epilogue for the vectors q = tid + 512 i it owns (all global accesses
-//    lane-coalesced), then releases the stage.
-// All waits are bounded (2 s); on timeout the error flag is raised, warp 0
-// waits for the copies it issued, and the kernel returns.
+//  * warp 8 (producer) fills a 2-stage shared-memory ring with tiles of u and
+//    a third stage with the tile of the elementwise stream (previous Lanczos
+//    vector in the first pass, partial sum later), all by TMA
+//    (cp.async.bulk.tensor, completion on mbarriers), and builds the first
+//    pass's per-tile diagonal tables;
+//  * warps 0..7 (consumers) own the vectors q = tid + 256 i (i < 16) of a
+//    tile: flips of the amplitude bit inside a vector and of the four bits of
+//    i are formed in registers, flips of the eight bits of tid from shared
+//    memory; the stream is read from its stage; results go to global memory
+//    with lane-coalesced stores.
+// All waits are bounded (2 s); on timeout the error flag is raised, the
+// producer waits for the copies it issued, and the kernel returns.
 template <typename T>
 __global__ void __launch_bounds__(kHpsiThreads, 1)
     hpsi_pass_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
@@ -216,19 +221,24 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     constexpr int LOGVE = Cx<T>::LOGVE;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    V *U = reinterpret_cast<V *>(smem_raw);
-    T *tab = reinterpret_cast<T *>(U + kStages * kTileV);
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(tab + kStages * kTab);
-    unsigned long long *empty = full + kStages;
+    V *U = reinterpret_cast<V *>(smem_raw);   // kStages tiles of u
+    V *S = U + kStages * kTileV;              // one tile of the stream
+    T *tab = reinterpret_cast<T *>(S + kTileV);
+    unsigned long long *fullU = reinterpret_cast<unsigned long long *>(tab + kStages * kTab);
+    unsigned long long *emptyU = fullU + kStages;
+    unsigned long long *fullS = emptyU + kStages;
+    unsigned long long *emptyS = fullS + 1;
 
     if (p.m_eff != nullptr && *p.m_eff <= p.stop_index) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&fullU[s], 1);
+            mbar_init(&emptyU[s], kConsumerWarps);
         }
+        mbar_init(fullS, 1);
+        mbar_init(emptyS, kConsumerWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -254,51 +264,81 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         }
     };
 
-    // Warp 0 issues the copies: tile n goes to stage n % kStages once all warps
-    // have released that stage's previous tile (n - kStages).
-    auto fill = [&](long long n, long long t) -> bool {
-        const int s = (int)(n % kStages);
-        if (n >= kStages) {
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(&empty[s], (unsigned)(((n / kStages) & 1) ^ 1), p.err);
-            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) return false;
-        }
-        if (p.first) {
-            // diagonal tables of tile t: TA[x] = E_hh + sum_{j<ta} s_j(x) F_j, TB[y] = sum s_j(y) F_{ta+j}
-            const int a = p.g, ta = p.ta, tb = a - ta;
-            const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
-            T *tb_s = tab + s * kTab;
-            for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
-                if (x < (1 << ta)) {
-                    T v = F[a];
-                    for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
-                    tb_s[x] = v;
-                } else {
-                    const int y = x - (1 << ta);
-                    T v = (T)0;
-                    for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
-                    tb_s[64 + y] = v;
-                }
+    if (warp == kConsumerWarps) {
+        // ------------------------------ producer ------------------------------
+        long long n = 0, nu = 0, ns = 0;  // tiles, u copies and stream copies issued
+        bool ok = true;
+        auto issue_u = [&](long long k, long long t) -> bool {
+            const int s = (int)(k % kStages);
+            if (k >= kStages) {
+                bool w = true;
+                if (lane == 0) w = mbar_wait(&emptyU[s], (unsigned)(((k / kStages) & 1) ^ 1), p.err);
+                if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
             }
-            __syncwarp();
+            if (p.first) {
+                // diagonal tables of tile t: TA[x] = E_hh + sum_{j<ta} s_j(x) F_j, TB[y] = sum s_j(y) F_{ta+j}
+                const int a = p.g, ta = p.ta, tb = a - ta;
+                const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
+                T *tb_s = tab + s * kTab;
+                for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
+                    if (x < (1 << ta)) {
+                        T v = F[a];
+                        for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
+                        tb_s[x] = v;
+                    } else {
+                        const int y = x - (1 << ta);
+                        T v = (T)0;
+                        for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
+                        tb_s[64 + y] = v;
+                    }
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                int crd[5];
+                coords(t, crd);
+                mbar_arrive_expect_tx(&fullU[s], p.tile_bytes);
+                tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &fullU[s]);
+            }
+            return true;
+        };
+        auto issue_s = [&](long long k, long long t) -> bool {
+            if (k >= 1) {
+                bool w = true;
+                if (lane == 0) w = mbar_wait(emptyS, (unsigned)(((k - 1) & 1)), p.err);
+                if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
+            }
+            if (lane == 0) {
+                int crd[5];
+                coords(t, crd);
+                mbar_arrive_expect_tx(fullS, p.tile_bytes);
+                tma_load(S, &tm_s, p.rank, crd, fullS);
+            }
+            return true;
+        };
+        // prologue: u for the first kStages tiles, stream for the first tile
+        for (long long t = blockIdx.x; t < p.ntiles && nu < kStages; t += gridDim.x) ok = ok && issue_u(nu++, t);
+        if (ok && has_stream && blockIdx.x < p.ntiles) ok = issue_s(ns++, blockIdx.x);
+        // steady state: while tile n is computed, u of tile n+kStages and the
+        // stream of tile n+1 are fetched as soon as their stages are released
+        for (long long t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++n) {
+            const long long tu = t + (long long)kStages * gridDim.x;
+            if (tu < p.ntiles) ok = issue_u(nu++, tu);
+            const long long ts = t + gridDim.x;
+            if (ok && has_stream && ts < p.ntiles) ok = issue_s(ns++, ts);
         }
         if (lane == 0) {
-            int crd[5];
-            coords(t, crd);
-            mbar_arrive_expect_tx(&full[s], p.tile_bytes);
-            tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &full[s]);
-            if (has_stream) tma_prefetch_l2(&tm_s, p.rank, crd);
+            if (!ok) atomicExch(p.err, 1);
+            // every copy this CTA issued has landed before it exits
+            const long long fu = nu > kStages ? nu - kStages : 0;
+            for (long long k = fu; k < nu; ++k)
+                mbar_wait(&fullU[(int)(k % kStages)], (unsigned)((k / kStages) & 1), p.err);
+            if (ns > 0) mbar_wait(fullS, (unsigned)((ns - 1) & 1), p.err);
         }
-        return true;
-    };
-    long long issued = 0;  // tiles whose copies warp 0 has issued
-    if (warp == 0) {
-        for (long long t = blockIdx.x; t < p.ntiles && issued < kStages; t += gridDim.x) {
-            fill(issued, t);
-            ++issued;
-        }
+        return;
     }
 
+    // ------------------------------ consumers ------------------------------
     const int tid = threadIdx.x;
     double sv = 1.0, ea = 0.0, eb = 0.0;
     if (p.epi != nullptr) {
@@ -306,192 +346,183 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         ea = p.epi[1];
         eb = p.epi[2];
     }
-    // first pass: r = H_inner u - a u - (b/sv) uprev ;  last pass: w = sv * r
+    // first pass: r = H_inner u - a u + bs uprev with bs = -b/sv; later: r = flips + partial
     const T aT = (T)ea;
-    // stream coefficient bs: -b/sv for the previous vector in the first pass, 1 for a partial sum
-    const double bs = (p.first && has_stream) ? -eb / sv : 1.0;
-    const bool use_stream = has_stream && bs != 0.0;
-    const T kap = use_stream ? (T)(1.0 / bs) : (T)1, ikap = use_stream ? (T)bs : (T)1;
+    const T bsT = (p.first && has_stream) ? (T)(-eb / sv) : (T)1;
     const T svT = (T)sv;
     const int nmine =
         tid < nvec ? ((nvec - 1 - tid) / kPassThreads + 1 < kBV ? (nvec - 1 - tid) / kPassThreads + 1 : kBV) : 0;
+    const bool full_tile = (nmine == kBV);
     auto gidx = [&](uint64_t base, int q) -> uint64_t {  // global 16-byte vector index of tile vector q
         const int li = q << LOGVE;
         return (base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask)) >> LOGVE;
     };
 
-    // E_ll of this thread's amplitudes: they sit at the same low bits in every
-    // tile of the first pass, so the table is read once per launch
-    T ell[kBV * VE];
-#pragma unroll
-    for (int e = 0; e < kBV * VE; ++e) {
-        const int li = (((e / VE) * kPassThreads + tid) << LOGVE) + (e % VE);
-        ell[e] = (p.first && li < (nvec << LOGVE)) ? __ldg(&p.Ell[li]) : (T)0;
-    }
     double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
     long long n = 0;
     bool failed = false;
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++n) {
         const int s = (int)(n % kStages);
-        const unsigned ph = (unsigned)((n / kStages) & 1);
-        if (warp == 0 && n >= 1) {
-            // refill the stage released by tile n-1 with tile n-1+kStages
-            const long long tf = blockIdx.x + (n - 1 + kStages) * (long long)gridDim.x;
-            if (issued == n - 1 + kStages && tf < p.ntiles) {
-                if (!fill(issued, tf)) {
-                    if (lane == 0) atomicExch(p.err, 1);
-                    failed = true;
-                    break;
-                }
-                ++issued;
-            }
-        }
         const V *Ucur = U + (size_t)s * kTileV;
         const T *tcur = tab + s * kTab;
         const uint64_t tt = (uint64_t)t;
         const uint64_t base = ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
-        if (!mbar_wait(&full[s], ph, p.err)) {
+        if (!mbar_wait(&fullU[s], (unsigned)((n / kStages) & 1), p.err)) {
             atomicExch(p.err, 1);
-            failed = true;
             break;
         }
-        T pd0 = 0, pd1 = 0, pn = 0;
-        const bool full_tile = (nmine == kBV);
-        // TA entries of this thread: the low ta bits of its amplitudes do not
-        // depend on the vector index i (512 << LOGVE >= 2^ta)
-        T ta_e[VE];
-        if (p.first) {
-#pragma unroll
-            for (int e = 0; e < VE; ++e) ta_e[e] = tcur[((tid << LOGVE) + e) & ((1 << p.ta) - 1)];
-        }
-        // The accumulators start from the elementwise stream (partial sum, or
-        // the previous Lanczos vector); flip and diagonal coefficients are
-        // scaled by kap = 1/bs so that r / kap is the wanted sum.
-        A self[kBV * VE], r[kBV * VE];
-#pragma unroll
-        for (int i = 0; i < kBV; ++i) {
-            if (use_stream && (full_tile || i < nmine))
-                unpackv(__ldcs(&p.stream[gidx(base, i * kPassThreads + tid)]), &r[i * VE]);
-            else
-                unpackv(V{}, &r[i * VE]);
-        }
+        A self[kBV * VE];
 #pragma unroll
         for (int i = 0; i < kBV; ++i) {
             if (full_tile || i < nmine) unpackv(Ucur[i * kPassThreads + tid], &self[i * VE]);
             else unpackv(V{}, &self[i * VE]);
         }
-        // flips of bits held in registers: the amplitude bit inside a vector
-        // (first pass) and the three bits of the vector index i
-        if (VE == 2 && p.c == 0) {
-            const K f = mkcoef(p.hb[p.o] * kap);
+        const T *trow = tcur;
+        T pd0 = 0, pd1 = 0, pn = 0;
+        bool stream_ready = false;
+        // accumulate in two halves of eight vectors (all sixteen inputs stay in registers)
 #pragma unroll
-            for (int i = 0; i < kBV; ++i) {
-                afma(f, self[i * VE + VE - 1], r[i * VE]);
-                afma(f, self[i * VE], r[i * VE + VE - 1]);
+        for (int hh = 0; hh < 2; ++hh) {
+            constexpr int NH = kBV / 2;
+            A r[NH * VE];
+#pragma unroll
+            for (int e = 0; e < NH * VE; ++e) r[e] = azero(T(0));
+            // flips of bits held in registers: the amplitude bit inside a
+            // vector (first pass) and the four bits of the vector index i
+            if (VE == 2 && p.c == 0) {
+                const K f = mkcoef(p.hb[p.o]);
+#pragma unroll
+                for (int i = 0; i < NH; ++i) {
+                    const int ii = hh * NH + i;
+                    afma(f, self[ii * VE + VE - 1], r[i * VE]);
+                    afma(f, self[ii * VE], r[i * VE + VE - 1]);
+                }
             }
-        }
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int lb = LOGVE + 9 + j;  // local bit carried by bit j of i
-            if (lb >= p.c && lb < tbits) {
-                const K f = mkcoef(p.hb[p.o + lb - p.c] * kap);
+            for (int j = 0; j < kIBits; ++j) {
+                const int lb = LOGVE + kTBits + j;  // local bit carried by bit j of i
+                if (lb >= p.c && lb < tbits) {
+                    const K f = mkcoef(p.hb[p.o + lb - p.c]);
 #pragma unroll
-                for (int i = 0; i < kBV; ++i)
+                    for (int i = 0; i < NH; ++i) {
+                        const int ii = hh * NH + i;
 #pragma unroll
-                    for (int e = 0; e < VE; ++e) afma(f, self[(i ^ (1 << j)) * VE + e], r[i * VE + e]);
-            }
-        }
-        // flips of bits across threads: neighbour vectors from shared memory
-        {
-            const int lb0 = p.c > LOGVE ? p.c : LOGVE;
-            const int lb1 = tbits < LOGVE + 9 ? tbits : LOGVE + 9;
-            for (int lb = lb0; lb < lb1; ++lb) {
-                const K f = mkcoef(p.hb[p.o + lb - p.c] * kap);
-                const int flip = 1 << (lb - LOGVE);
-#pragma unroll
-                for (int h4 = 0; h4 < 2; ++h4) {
-                    V v[kHB];
-#pragma unroll
-                    for (int i = 0; i < kHB; ++i) {
-                        const int ii = h4 * kHB + i;
-                        if (full_tile || ii < nmine) v[i] = Ucur[(ii * kPassThreads + tid) ^ flip];
-                        else v[i] = V{};
+                        for (int e = 0; e < VE; ++e) afma(f, self[(ii ^ (1 << j)) * VE + e], r[i * VE + e]);
                     }
+                }
+            }
+            // flips of bits across threads: neighbour vectors from shared memory
+            {
+                const int lb0 = p.c > LOGVE ? p.c : LOGVE;
+                const int lb1 = tbits < LOGVE + kTBits ? tbits : LOGVE + kTBits;
+                for (int lb = lb0; lb < lb1; ++lb) {
+                    const K f = mkcoef(p.hb[p.o + lb - p.c]);
+                    const int flip = 1 << (lb - LOGVE);
 #pragma unroll
-                    for (int i = 0; i < kHB; ++i) {
+                    for (int h4 = 0; h4 < NH / kHB; ++h4) {
+                        V v[kHB];
+#pragma unroll
+                        for (int i = 0; i < kHB; ++i) {
+                            const int ii = hh * NH + h4 * kHB + i;
+                            if (full_tile || ii < nmine) v[i] = Ucur[(ii * kPassThreads + tid) ^ flip];
+                            else v[i] = V{};
+                        }
+#pragma unroll
+                        for (int i = 0; i < kHB; ++i) {
+                            A x[VE];
+                            unpackv(v[i], x);
+#pragma unroll
+                            for (int e = 0; e < VE; ++e) afma(f, x[e], r[(h4 * kHB + i) * VE + e]);
+                        }
+                    }
+                }
+            }
+            if (p.first) {
+                // E(b) - a = E_ll + TA (low ta bits) + TB (bits above ta) - a
+                const int tmask = (1 << p.ta) - 1;
+#pragma unroll
+                for (int i = 0; i < NH; ++i) {
+                    const int ii = hh * NH + i;
+                    if (full_tile || ii < nmine) {
+                        const int li = (ii * kPassThreads + tid) << LOGVE;
+                        const T tbv = trow[64 + (li >> p.ta)] - aT;
+#pragma unroll
+                        for (int e = 0; e < VE; ++e) {
+                            const T E = __ldg(&p.Ell[li + e]) + trow[(li + e) & tmask] + tbv;
+                            afma(mkcoef(E), self[ii * VE + e], r[i * VE + e]);
+                        }
+                    }
+                }
+            }
+            if (hh == 1) {
+                // u stage s is no longer read by this warp
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&emptyU[s]);
+            }
+            if (has_stream) {
+                if (!stream_ready) {
+                    if (!mbar_wait(fullS, (unsigned)(n & 1), p.err)) {
+                        atomicExch(p.err, 1);
+                        failed = true;
+                        break;
+                    }
+                    stream_ready = true;
+                }
+                const K bsK = mkcoef(bsT);
+#pragma unroll
+                for (int i = 0; i < NH; ++i) {
+                    const int ii = hh * NH + i;
+                    if (full_tile || ii < nmine) {
                         A x[VE];
-                        unpackv(v[i], x);
+                        unpackv(S[ii * kPassThreads + tid], x);
 #pragma unroll
-                        for (int e = 0; e < VE; ++e) afma(f, x[e], r[(h4 * kHB + i) * VE + e]);
+                        for (int e = 0; e < VE; ++e) afma(bsK, x[e], r[i * VE + e]);
+                    }
+                }
+                if (hh == 1) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(emptyS);
+                }
+            }
+            if (p.last && p.epilogue != EPI_ENERGY && svT != (T)1) {
+                const K svK = mkcoef(svT);
+#pragma unroll
+                for (int e = 0; e < NH * VE; ++e) amul(svK, r[e]);
+            }
+            if (!p.last || p.epilogue != EPI_ENERGY) {
+#pragma unroll
+                for (int i = 0; i < NH; ++i) {
+                    const int ii = hh * NH + i;
+                    if (full_tile || ii < nmine) {
+                        if (p.last) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], packv(&r[i * VE]));
+                        else p.out[gidx(base, ii * kPassThreads + tid)] = packv(&r[i * VE]);
                     }
                 }
             }
-        }
-        if (p.first) {
-            // (E(b) - a) kap = (E_ll + TA + TB - a) kap
+            if (p.last && p.epilogue == EPI_ENERGY) {
 #pragma unroll
-            for (int i = 0; i < kBV; ++i) {
-                if (full_tile || i < nmine) {
-                    const int li = (i * kPassThreads + tid) << LOGVE;
-                    const T tbv = tcur[64 + (li >> p.ta)] - aT;
+                for (int e = 0; e < NH * VE; ++e) {
+                    const auto u = tocx(self[hh * NH * VE + e]), w = tocx(r[e]);
+                    pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
+                    pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
+                    pn = fma(u.x, u.x, fma(u.y, u.y, pn));
+                }
+            } else if (p.last && p.epilogue == EPI_KRYLOV) {
 #pragma unroll
-                    for (int e = 0; e < VE; ++e) {
-                        const T E = (ell[i * VE + e] + ta_e[e] + tbv) * kap;
-                        afma(mkcoef(E), self[i * VE + e], r[i * VE + e]);
-                    }
+                for (int e = 0; e < NH * VE; ++e) {
+                    const auto u = tocx(self[hh * NH * VE + e]), w = tocx(r[e]);
+                    pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
+                    pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
+                    pn = fma(w.x, w.x, fma(w.y, w.y, pn));
                 }
             }
         }
-        // stage s is no longer read by this warp
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-
-        // r <- r / kap (and * sv in the last pass)
-        {
-            const T sc = (p.last && p.epilogue != EPI_ENERGY) ? ikap * svT : ikap;
-            if (sc != (T)1) {
-                const K scK = mkcoef(sc);
-#pragma unroll
-                for (int e = 0; e < kBV * VE; ++e) amul(scK, r[e]);
-            }
-        }
-        if (!p.last || p.epilogue == EPI_PLAIN || p.epilogue == EPI_KRYLOV) {
-#pragma unroll
-            for (int i = 0; i < kBV; ++i) {
-                if (full_tile || i < nmine) {
-                    if (p.last) st_stream(&p.out[gidx(base, i * kPassThreads + tid)], packv(&r[i * VE]));
-                    else p.out[gidx(base, i * kPassThreads + tid)] = packv(&r[i * VE]);
-                }
-            }
-        }
-        if (p.last && p.epilogue == EPI_ENERGY) {
-#pragma unroll
-            for (int e = 0; e < kBV * VE; ++e) {
-                const auto u = tocx(self[e]), w = tocx(r[e]);
-                pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
-                pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
-                pn = fma(u.x, u.x, fma(u.y, u.y, pn));
-            }
-        } else if (p.last && p.epilogue == EPI_KRYLOV) {
-#pragma unroll
-            for (int e = 0; e < kBV * VE; ++e) {
-                const auto u = tocx(self[e]), w = tocx(r[e]);
-                pd0 = fma(u.x, w.x, fma(u.y, w.y, pd0));
-                pd1 = fma(u.x, w.y, fma(-u.y, w.x, pd1));
-                pn = fma(w.x, w.x, fma(w.y, w.y, pn));
-            }
-        }
+        if (failed) break;
         acc_d0 += (double)pd0;
         acc_d1 += (double)pd1;
         acc_n += (double)pn;
     }
 
-    if (failed && warp == 0 && lane == 0) {
-        // every copy this CTA issued lands before it exits (bounded)
-        const long long first = issued > kStages ? issued - kStages : 0;
-        for (long long k = first; k < issued; ++k)
-            mbar_wait(&full[(int)(k % kStages)], (unsigned)((k / kStages) & 1), p.err);
-    }
     if (p.last && p.epilogue != EPI_PLAIN && p.partials != nullptr) {
         // per-warp partials (fixed order, no CTA barrier so early exits cannot hang)
 #pragma unroll
@@ -587,8 +618,8 @@ PassPlan make_plan(int L, int prec) {
 }
 
 static size_t pass_smem() {
-    return (size_t)kStages * (1u << kTileBytesLog2) + (size_t)kStages * kTab * sizeof(double) +
-           2 * kStages * sizeof(unsigned long long);
+    return (size_t)(kStages + 1) * (1u << kTileBytesLog2) + (size_t)kStages * kTab * sizeof(double) +
+           (2 * kStages + 2) * sizeof(unsigned long long);
 }
 
 template <typename T>
