@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&fullU[s], 1);
+            // first pass: the tile's copy and its diagonal tables are two arrivals
+            mbar_init(&fullU[s], p.first ? 2 : 1);
             mbar_init(&emptyU[s], kConsumerWarps);
         }
         mbar_init(fullS, 1);
@@ -275,8 +276,15 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 if (lane == 0) w = mbar_wait(&emptyU[s], (unsigned)(((k / kStages) & 1) ^ 1), p.err);
                 if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
             }
+            if (lane == 0) {
+                int crd[5];
+                coords(t, crd);
+                mbar_arrive_expect_tx(&fullU[s], p.tile_bytes);
+                tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &fullU[s]);
+            }
             if (p.first) {
-                // diagonal tables of tile t: TA[x] = E_hh + sum_{j<ta} s_j(x) F_j, TB[y] = sum s_j(y) F_{ta+j}
+                // diagonal tables of tile t (built while its copy is in flight):
+                // TA[x] = E_hh + sum_{j<ta} s_j(x) F_j,  TB[y] = sum_j s_j(y) F_{ta+j}
                 const int a = p.g, ta = p.ta, tb = a - ta;
                 const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
                 T *tb_s = tab + s * kTab;
@@ -293,12 +301,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                     }
                 }
                 __syncwarp();
-            }
-            if (lane == 0) {
-                int crd[5];
-                coords(t, crd);
-                mbar_arrive_expect_tx(&fullU[s], p.tile_bytes);
-                tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &fullU[s]);
+                if (lane == 0) mbar_arrive(&fullU[s]);  // second arrival: tables written
             }
             return true;
         };
