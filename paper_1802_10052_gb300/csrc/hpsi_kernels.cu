@@ -54,7 +54,7 @@ template <> struct Cx<double> {
 constexpr int kBV = 16;                                 // 16-byte vectors per consumer thread per tile
 constexpr int kHB = kBV / 2;                            // processed in two halves
 constexpr int kTileV = 1 << (kTileBytesLog2 - 4);       // 16-byte vectors per tile
-constexpr int kTab = 256;                               // TA (<= 64) + TB (<= 128) per stage
+constexpr int kTab = 192;                               // TA (<= 64) + TB (<= 128) per stage
 constexpr int kStages = 2;                              // shared-memory ring of u tiles
 constexpr int kConsumerWarps = kPassThreads / 32;       // 8
 constexpr int kIBits = 4;                               // log2 kBV: vector-index bits held in registers
@@ -79,8 +79,6 @@ struct PassParams {
     int L, c, o, g, ta, first, last, epilogue, rank;
     unsigned tile_bytes;
     T hb[kMaxL + 1];
-    T Jr[kMaxL + 1];                    // J(r) (first pass: in-tile diagonal)
-    T EV[32];                           // first pass: energy of the pairs among the register bits
 };
 
 __device__ __forceinline__ void unpackv(const ulonglong2 &v, unsigned long long *a) {
@@ -197,6 +195,18 @@ __device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap *tm, int rank,
 template <typename V>
 __device__ __forceinline__ void st_stream(V *ptr, const V &v) {
     __stcs(ptr, v);
+}
+// read-only table load that asks L1 to keep the line (the E_ll table is
+// re-read by every tile of the first pass)
+__device__ __forceinline__ float ld_keep(const float *ptr) {
+    float v;
+    asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(ptr));
+    return v;
+}
+__device__ __forceinline__ double ld_keep(const double *ptr) {
+    double v;
+    asm("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(ptr));
+    return v;
 }
 
 // One pass of the product, warp-specialized and persistent (one CTA per SM):
@@ -363,35 +373,6 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         return (base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask)) >> LOGVE;
     };
 
-    // In-tile diagonal E_ll(lo) of the first pass.  The low bits of an
-    // amplitude are the amplitude bit inside its vector (bit 0, complex64 only),
-    // the eight bits of tid (F) and the four bits of i (V, with bit 0): every
-    // thread sees the same lo values in every tile, and
-    //   E_ll = C(tid) + EV(v) + sum_{j in V} s_j(v) G_j(tid),
-    //   C = sum of the pairs inside F, G_j = sum_{k in F} J(|k - j|) s_k.
-    constexpr int NV = kIBits + LOGVE;  // register bits
-    T Cf = (T)0, G[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) G[j] = (T)0;
-    if (p.first) {
-        for (int m = 0; m < kTBits; ++m) {
-            const int pk = LOGVE + m;
-            if (pk >= tbits) break;
-            const T sk = ((tid >> m) & 1) ? (T)-1 : (T)1;
-            for (int m2 = m + 1; m2 < kTBits; ++m2) {
-                const int pk2 = LOGVE + m2;
-                if (pk2 >= tbits) break;
-                const T sk2 = ((tid >> m2) & 1) ? (T)-1 : (T)1;
-                Cf += p.Jr[pk2 - pk] * sk * sk2;
-            }
-#pragma unroll
-            for (int j = 0; j < NV; ++j) {
-                const int pj = (LOGVE == 1 && j == 0) ? 0 : LOGVE + kTBits + (j - LOGVE);
-                if (pj < tbits) G[j] += p.Jr[pj > pk ? pj - pk : pk - pj] * sk;
-            }
-        }
-    }
-
     double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
     long long n = 0;
     bool failed = false;
@@ -482,10 +463,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                         const T tbv = trow[64 + (li >> p.ta)] - aT;
 #pragma unroll
                         for (int e = 0; e < VE; ++e) {
-                            const int v = (ii << LOGVE) | e;  // register bits of this amplitude
-                            T E = Cf + p.EV[v] + trow[(li + e) & tmask] + tbv;
-#pragma unroll
-                            for (int j = 0; j < NV; ++j) E += ((v >> j) & 1) ? -G[j] : G[j];
+                            const T E = ld_keep(&p.Ell[li + e]) + trow[(li + e) & tmask] + tbv;
                             afma(mkcoef(E), self[ii * VE + e], r[i * VE + e]);
                         }
                     }
@@ -664,6 +642,14 @@ static int grid_for(Handle *h, long long ntiles) {
     static int occ = -1;
     if (occ < 0) {
         cudaFuncSetAttribute(hpsi_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem());
+        // smallest shared-memory carve-out that fits (the rest stays L1 for the E_ll table)
+        int maxsm = 0;
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+        if (maxsm > 0) {
+            int pct = (int)((pass_smem() + 2048) * 100 / (size_t)maxsm) + 1;
+            if (pct > 100) pct = 100;
+            cudaFuncSetAttribute(hpsi_pass_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        }
         int n = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hpsi_pass_kernel<T>, kHpsiThreads, pass_smem());
         occ = n > 0 ? n : 1;
@@ -831,31 +817,7 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.epilogue = a.epilogue;
         p.rank = rank;
         p.tile_bytes = (unsigned)((1u << (d.c + d.g)) * h->esize);
-        for (int k = 0; k <= kMaxL; ++k) {
-            p.hb[k] = (T)h->hbit[k];
-            p.Jr[k] = (T)h->Jr[k];
-        }
-        if (d.first) {
-            // pairs among the register bits: bit 0 (complex64) and the four
-            // vector-index bits above the eight thread bits
-            const int logve = Cx<T>::LOGVE, nv = kIBits + logve;
-            int pos[8];
-            for (int j = 0; j < nv; ++j) pos[j] = (logve == 1 && j == 0) ? 0 : logve + kTBits + (j - logve);
-            for (int v = 0; v < 32; ++v) {
-                double e = 0.0;
-                if (v < (1 << nv)) {
-                    for (int j = 0; j < nv; ++j) {
-                        if (pos[j] >= d.c + d.g) continue;
-                        for (int j2 = j + 1; j2 < nv; ++j2) {
-                            if (pos[j2] >= d.c + d.g) continue;
-                            const int sj = ((v >> j) & 1) ? -1 : 1, sj2 = ((v >> j2) & 1) ? -1 : 1;
-                            e += h->Jr[pos[j2] - pos[j]] * sj * sj2;
-                        }
-                    }
-                }
-                p.EV[v] = (T)e;
-            }
-        }
+        for (int k = 0; k <= kMaxL; ++k) p.hb[k] = (T)h->hbit[k];
         const int grid = grid_for<T>(h, d.ntiles);
         hpsi_pass_kernel<T><<<grid, kHpsiThreads, pass_smem(), h->stream>>>(tm_u, tm_s, p);
         h->launches += 1;
