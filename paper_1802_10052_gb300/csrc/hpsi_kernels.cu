@@ -59,7 +59,7 @@ constexpr int kStages = 2;                              // shared-memory ring of
 constexpr int kConsumerWarps = kPassThreads / 32;       // 8
 constexpr int kIBits = 4;                               // log2 kBV: vector-index bits held in registers
 constexpr int kTBits = 8;                               // log2 kPassThreads
-constexpr int kHpsiThreads = kPassThreads + 32;         // + one producer warp
+constexpr int kHpsiThreads = kPassThreads;              // warp 0 also issues the copies
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 static_assert(kTileV == kBV * kPassThreads && (1 << kIBits) == kBV && (1 << kTBits) == kPassThreads,
               "sixteen vectors per consumer thread per tile");
@@ -210,18 +210,18 @@ __device__ __forceinline__ double ld_keep(const double *ptr) {
 }
 
 // One pass of the product, warp-specialized and persistent (one CTA per SM):
-//  * warp 8 (producer) fills a 2-stage shared-memory ring with tiles of u and
-//    a third stage with the tile of the elementwise stream (previous Lanczos
-//    vector in the first pass, partial sum later), all by TMA
-//    (cp.async.bulk.tensor, completion on mbarriers), and builds the first
-//    pass's per-tile diagonal tables;
-//  * warps 0..7 (consumers) own the vectors q = tid + 256 i (i < 16) of a
+//  * warp 0 fills a 2-stage shared-memory ring with tiles of u and a third
+//    stage with the tile of the elementwise stream (previous Lanczos vector in
+//    the first pass, partial sum later), all by TMA (cp.async.bulk.tensor,
+//    completion on mbarriers), as soon as the stage is released, and builds
+//    the first pass's per-tile diagonal tables;
+//  * all 8 warps own the vectors q = tid + 256 i (i < 16) of a
 //    tile: flips of the amplitude bit inside a vector and of the four bits of
 //    i are formed in registers, flips of the eight bits of tid from shared
 //    memory; the stream is read from its stage; results go to global memory
 //    with lane-coalesced stores.
-// All waits are bounded (2 s); on timeout the error flag is raised, the
-// producer waits for the copies it issued, and the kernel returns.
+// All waits are bounded (2 s); on timeout the error flag is raised, warp 0
+// waits for the copies it issued, and the kernel returns.
 template <typename T>
 __global__ void __launch_bounds__(kHpsiThreads, 1)
     hpsi_pass_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
@@ -277,80 +277,63 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         }
     };
 
-    if (warp == kConsumerWarps) {
-        // ------------------------------ producer ------------------------------
-        long long n = 0, nu = 0, ns = 0;  // tiles, u copies and stream copies issued
-        bool ok = true;
-        auto issue_u = [&](long long k, long long t) -> bool {
-            const int s = (int)(k % kStages);
-            if (k >= kStages) {
-                bool w = true;
-                if (lane == 0) w = mbar_wait(&emptyU[s], (unsigned)(((k / kStages) & 1) ^ 1), p.err);
-                if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
-            }
-            if (lane == 0) {
-                int crd[5];
-                coords(t, crd);
-                mbar_arrive_expect_tx(&fullU[s], p.tile_bytes);
-                tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &fullU[s]);
-            }
-            if (p.first) {
-                // diagonal tables of tile t (built while its copy is in flight):
-                // TA[x] = E_hh + sum_{j<ta} s_j(x) F_j,  TB[y] = sum_j s_j(y) F_{ta+j}
-                const int a = p.g, ta = p.ta, tb = a - ta;
-                const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
-                T *tb_s = tab + s * kTab;
-                for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
-                    if (x < (1 << ta)) {
-                        T v = F[a];
-                        for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
-                        tb_s[x] = v;
-                    } else {
-                        const int y = x - (1 << ta);
-                        T v = (T)0;
-                        for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
-                        tb_s[64 + y] = v;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&fullU[s]);  // second arrival: tables written
-            }
-            return true;
-        };
-        auto issue_s = [&](long long k, long long t) -> bool {
-            if (k >= 1) {
-                bool w = true;
-                if (lane == 0) w = mbar_wait(emptyS, (unsigned)(((k - 1) & 1)), p.err);
-                if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
-            }
-            if (lane == 0) {
-                int crd[5];
-                coords(t, crd);
-                mbar_arrive_expect_tx(fullS, p.tile_bytes);
-                tma_load(S, &tm_s, p.rank, crd, fullS);
-            }
-            return true;
-        };
-        // prologue: u for the first kStages tiles, stream for the first tile
-        for (long long t = blockIdx.x; t < p.ntiles && nu < kStages; t += gridDim.x) ok = ok && issue_u(nu++, t);
-        if (ok && has_stream && blockIdx.x < p.ntiles) ok = issue_s(ns++, blockIdx.x);
-        // steady state: while tile n is computed, u of tile n+kStages and the
-        // stream of tile n+1 are fetched as soon as their stages are released
-        for (long long t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x, ++n) {
-            const long long tu = t + (long long)kStages * gridDim.x;
-            if (tu < p.ntiles) ok = issue_u(nu++, tu);
-            const long long ts = t + gridDim.x;
-            if (ok && has_stream && ts < p.ntiles) ok = issue_s(ns++, ts);
+    // Copies are issued by warp 0: u of tile k into stage k % kStages once all
+    // warps released the stage's previous tile, the stream of tile k once all
+    // warps consumed the stream of tile k-1.
+    long long nu = 0, ns = 0;
+    auto issue_u = [&](long long k, long long t) -> bool {
+        const int s = (int)(k % kStages);
+        if (k >= kStages) {
+            bool w = true;
+            if (lane == 0) w = mbar_wait(&emptyU[s], (unsigned)(((k / kStages) & 1) ^ 1), p.err);
+            if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
         }
         if (lane == 0) {
-            if (!ok) atomicExch(p.err, 1);
-            // every copy this CTA issued has landed before it exits
-            const long long fu = nu > kStages ? nu - kStages : 0;
-            for (long long k = fu; k < nu; ++k)
-                mbar_wait(&fullU[(int)(k % kStages)], (unsigned)((k / kStages) & 1), p.err);
-            if (ns > 0) mbar_wait(fullS, (unsigned)((ns - 1) & 1), p.err);
+            int crd[5];
+            coords(t, crd);
+            mbar_arrive_expect_tx(&fullU[s], p.tile_bytes);
+            tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &fullU[s]);
         }
-        return;
+        if (p.first) {
+            // diagonal tables of tile t (built while its copy is in flight):
+            // TA[x] = E_hh + sum_{j<ta} s_j(x) F_j,  TB[y] = sum_j s_j(y) F_{ta+j}
+            const int a = p.g, ta = p.ta, tb = a - ta;
+            const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
+            T *tb_s = tab + s * kTab;
+            for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
+                if (x < (1 << ta)) {
+                    T v = F[a];
+                    for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
+                    tb_s[x] = v;
+                } else {
+                    const int y = x - (1 << ta);
+                    T v = (T)0;
+                    for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
+                    tb_s[64 + y] = v;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&fullU[s]);  // second arrival: tables written
+        }
+        return true;
+    };
+    auto issue_s = [&](long long k, long long t) -> bool {
+        if (k >= 1) {
+            bool w = true;
+            if (lane == 0) w = mbar_wait(emptyS, (unsigned)((k - 1) & 1), p.err);
+            if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) return false;
+        }
+        if (lane == 0) {
+            int crd[5];
+            coords(t, crd);
+            mbar_arrive_expect_tx(fullS, p.tile_bytes);
+            tma_load(S, &tm_s, p.rank, crd, fullS);
+        }
+        return true;
+    };
+    if (warp == 0) {
+        for (long long t = blockIdx.x; t < p.ntiles && nu < kStages; t += gridDim.x) issue_u(nu++, t);
+        if (has_stream && blockIdx.x < p.ntiles) issue_s(ns++, blockIdx.x);
     }
 
     // ------------------------------ consumers ------------------------------
@@ -373,11 +356,31 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         return (base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask)) >> LOGVE;
     };
 
+    // E_ll of this thread's amplitudes: they sit at the same low bits in every
+    // tile of the first pass, so the table is read once per launch
+    T ell[kBV * VE];
+#pragma unroll
+    for (int e = 0; e < kBV * VE; ++e) {
+        const int li = (((e / VE) * kPassThreads + tid) << LOGVE) + (e % VE);
+        ell[e] = (p.first && li < (nvec << LOGVE)) ? __ldg(&p.Ell[li]) : (T)0;
+    }
     double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
     long long n = 0;
     bool failed = false;
     for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++n) {
         const int s = (int)(n % kStages);
+        if (warp == 0 && n >= 1) {
+            // u of tile n-1+kStages into the stage released by tile n-1; stream of tile n
+            const long long tu = t + (long long)(kStages - 1) * gridDim.x;
+            bool ok = true;
+            if (nu == n - 1 + kStages && tu < p.ntiles) ok = issue_u(nu++, tu);
+            if (ok && has_stream && ns == n) ok = issue_s(ns++, t);
+            if (!ok) {
+                if (lane == 0) atomicExch(p.err, 1);
+                failed = true;
+                break;
+            }
+        }
         const V *Ucur = U + (size_t)s * kTileV;
         const T *tcur = tab + s * kTab;
         const uint64_t tt = (uint64_t)t;
@@ -386,25 +389,25 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             atomicExch(p.err, 1);
             break;
         }
+        const T *trow = tcur;
+        T pd0 = 0, pd1 = 0, pn = 0;
+        bool stream_ready = false;
         A self[kBV * VE];
 #pragma unroll
         for (int i = 0; i < kBV; ++i) {
             if (full_tile || i < nmine) unpackv(Ucur[i * kPassThreads + tid], &self[i * VE]);
             else unpackv(V{}, &self[i * VE]);
         }
-        const T *trow = tcur;
-        T pd0 = 0, pd1 = 0, pn = 0;
-        bool stream_ready = false;
-        // accumulate in two halves of eight vectors (all sixteen inputs stay in registers)
+        // accumulate in two halves of eight vectors; all four bits of i are
+        // flipped in registers
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             constexpr int NH = kBV / 2;
             A r[NH * VE];
 #pragma unroll
             for (int e = 0; e < NH * VE; ++e) r[e] = azero(T(0));
-            // flips of bits held in registers: the amplitude bit inside a
-            // vector (first pass) and the four bits of the vector index i
             if (VE == 2 && p.c == 0) {
+                // bit 0 lives inside the 16-byte vector
                 const K f = mkcoef(p.hb[p.o]);
 #pragma unroll
                 for (int i = 0; i < NH; ++i) {
@@ -426,7 +429,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                     }
                 }
             }
-            // flips of bits across threads: neighbour vectors from shared memory
+            // flips of the eight bits of tid: neighbour vectors from shared memory
             {
                 const int lb0 = p.c > LOGVE ? p.c : LOGVE;
                 const int lb1 = tbits < LOGVE + kTBits ? tbits : LOGVE + kTBits;
@@ -453,7 +456,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
             if (p.first) {
-                // E(b) - a = E_ll + TA (low ta bits) + TB (bits above ta) - a
+                // E(b) - a = E_ll (registers) + TA (low ta bits) + TB (bits above ta) - a
                 const int tmask = (1 << p.ta) - 1;
 #pragma unroll
                 for (int i = 0; i < NH; ++i) {
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                         const T tbv = trow[64 + (li >> p.ta)] - aT;
 #pragma unroll
                         for (int e = 0; e < VE; ++e) {
-                            const T E = ld_keep(&p.Ell[li + e]) + trow[(li + e) & tmask] + tbv;
+                            const T E = ell[ii * VE + e] + trow[(li + e) & tmask] + tbv;
                             afma(mkcoef(E), self[ii * VE + e], r[i * VE + e]);
                         }
                     }
@@ -538,6 +541,13 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         acc_n += (double)pn;
     }
 
+    if (failed && warp == 0 && lane == 0) {
+        // every copy this CTA issued lands before it exits (bounded)
+        const long long fu = nu > kStages ? nu - kStages : 0;
+        for (long long k = fu; k < nu; ++k)
+            mbar_wait(&fullU[(int)(k % kStages)], (unsigned)((k / kStages) & 1), p.err);
+        if (ns > 0) mbar_wait(fullS, (unsigned)((ns - 1) & 1), p.err);
+    }
     if (p.last && p.epilogue != EPI_PLAIN && p.partials != nullptr) {
         // per-warp partials (fixed order, no CTA barrier so early exits cannot hang)
 #pragma unroll
