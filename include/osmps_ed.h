@@ -107,6 +107,13 @@ osmps_status osmps_ed_set_site_fields(osmps_ed_t *ed, const double *h_sites);
  * (initially 0). */
 osmps_status osmps_ed_set_reorth(osmps_ed_t *ed, int mode);
 
+/* Gram product of osmps_ed_schmidt_entropy: 0 = automatic (tensor cores,
+ * tcgen05 with a 3xTF32 split, for OSMPS_MIXED states whose left block has
+ * at least 128 rows and at most as many rows as columns; CUDA cores
+ * otherwise), 1 = CUDA cores, 2 = tensor cores (EUNSUPPORTED where they do
+ * not apply).  Not from the paper (implementation choice). */
+osmps_status osmps_ed_set_gram_mode(osmps_ed_t *ed, int mode);
+
 /* D = 2^L. */
 osmps_status osmps_ed_dim(const osmps_ed_t *ed, uint64_t *D);
 

@@ -96,6 +96,10 @@ class Chain:
     def set_reorth(self, mode):
         check(lib.osmps_ed_set_reorth(self._h, int(mode)), "osmps_ed_set_reorth")
 
+    def set_gram_mode(self, mode):
+        """0 automatic, 1 CUDA cores, 2 tensor cores (tcgen05, 3xTF32; complex64 only)."""
+        check(lib.osmps_ed_set_gram_mode(self._h, int(mode)), "osmps_ed_set_gram_mode")
+
     def timing_enable(self, on=True):
         check(lib.osmps_ed_timing_enable(self._h, 1 if on else 0), "osmps_ed_timing_enable")
 

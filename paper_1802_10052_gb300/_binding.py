@@ -29,6 +29,7 @@ SIGNATURES = {
     "osmps_ed_set_field": (_I, [_P, _D]),
     "osmps_ed_set_site_fields": (_I, [_P, _DP]),
     "osmps_ed_set_reorth": (_I, [_P, _I]),
+    "osmps_ed_set_gram_mode": (_I, [_P, _I]),
     "osmps_ed_dim": (_I, [_P, C.POINTER(_U64)]),
     "osmps_ed_device_bytes": (_I, [_P, C.POINTER(_U64)]),
     "osmps_ed_init_basis_state": (_I, [_P, _P, _U64]),

@@ -246,6 +246,7 @@ void destroy_handle(Handle *h) {
     }
     dev_free(h, h->V_dev, 0);
     dev_free(h, h->gram, 0);
+    dev_free(h, h->gram_aux, 0);
     dev_free(h, h->solver_ws, 0);
     dev_free(h, h->lam_dev, 0);
 }
@@ -437,6 +438,12 @@ osmps_status osmps_ed_set_reorth(osmps_ed_t *ed, int mode) {
     if (ed == nullptr || (mode != 0 && mode != 1)) return OSMPS_EINVAL;
     ed->h.reorth = mode;
     ed->reorth_set = true;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_gram_mode(osmps_ed_t *ed, int mode) {
+    if (ed == nullptr || mode < 0 || mode > 2) return OSMPS_EINVAL;
+    ed->h.gram_mode = mode;
     return OSMPS_OK;
 }
 
@@ -671,7 +678,14 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
         h->lam_cap = n + 1;
     }
     int nn = 0;
-    CK(launch_gram(h, psi, cut, h->gram, &nn));
+    {
+        const cudaError_t ge = launch_gram(h, psi, cut, h->gram, &nn);
+        if (ge == cudaErrorNotSupported) {
+            cudaGetLastError();
+            return OSMPS_EUNSUPPORTED;
+        }
+        CK(ge);
+    }
     CKS(schmidt_eig(h, h->gram, nn, h->lam_dev, h->lam_dev + nn));
     if (lambda) CK(cudaMemcpyAsync(lambda, h->lam_dev, sizeof(double) * nn, cudaMemcpyDeviceToHost, h->stream));
     double Sv = 0.0;

@@ -109,6 +109,10 @@ int vec_grid(Handle *h);
 // measure_kernels.cu
 cudaError_t launch_zstats(Handle *h, const void *psi, double *out_dev);
 cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_out);
+
+// gram_tc.cu (tensor-core Gram product, complex64 only)
+bool gram_tc_supported(int n, long long K);
+cudaError_t gram_tc_launch(Handle *h, const void *psi, int n, long long K, void *rho, float *planes, float *G);
 osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev);
 
 // Device memory owned by a handle.
@@ -145,6 +149,9 @@ struct Handle {
     int Vcap;                   // allocated vectors (excluding V[0])
     void *gram;                 // Gram matrix buffer
     size_t gram_bytes;
+    void *gram_aux;             // tensor-core Gram: TF32 hi/lo planes and G
+    size_t gram_aux_bytes;
+    int gram_mode;              // 0 automatic, 1 CUDA cores, 2 tensor cores
     void *solver_ws;            // cuSOLVER workspace
     size_t solver_ws_bytes;
     double *lam_dev;

@@ -376,6 +376,24 @@ cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_o
         sk = n;
     }
     *n_out = n;
+    // tensor cores (tcgen05, 3xTF32) for complex64 rows; CUDA cores otherwise
+    const bool tc_ok = (h->prec == OSMPS_MIXED) && (sk == 1) && gram_tc_supported(n, K);
+    if (h->gram_mode == 2 && !tc_ok) return cudaErrorNotSupported;
+    if (tc_ok && h->gram_mode != 1) {
+        const size_t need = sizeof(float) * ((size_t)n * 4 * (size_t)K + (size_t)n * n);
+        if (need > h->gram_aux_bytes) {
+            dev_free(h, h->gram_aux, h->gram_aux_bytes);
+            h->gram_aux = nullptr;
+            h->gram_aux_bytes = 0;
+            cudaError_t err;
+            h->gram_aux = dev_alloc(h, need, &err);
+            if (err != cudaSuccess) return err;
+            h->gram_aux_bytes = need;
+        }
+        float *planes = (float *)h->gram_aux;
+        float *G = planes + (size_t)n * 4 * (size_t)K;
+        return gram_tc_launch(h, psi, n, K, rho, planes, G);
+    }
     dim3 grid((n + kGT - 1) / kGT, (n + kGT - 1) / kGT);
     if (h->prec == OSMPS_FP64)
         gram_kernel<double><<<grid, 256, 0, h->stream>>>((const double2 *)psi, n, K, sx, sk, (double2 *)rho);

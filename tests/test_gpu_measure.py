@@ -95,3 +95,38 @@ def test_page_value_L20(prec):
     assert abs(S - page) < 2e-3
     assert abs(lam.sum() - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
     assert lam.min() > -1e-6
+
+
+@pytest.mark.parametrize("L,cut", [(14, -1), (15, 7), (16, -1), (18, 8), (19, -1)])
+def test_tensor_core_gram_matches_oracle(L, cut):
+    """Half-chain spectrum with the Gram product on the tensor cores (tcgen05,
+    3xTF32) against the oracle's eigvalsh(M M^dagger), and against the CUDA-core
+    Gram product of the same state."""
+    psi = si.gaussian_state(L, 80 + L)
+    x = to_dev(psi, "mixed")
+    ref_state = x.cpu().numpy().astype(np.complex128)
+    l = L // 2 if cut == -1 else cut
+    want = O.schmidt_spectrum(ref_state, L, l)
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec="mixed")
+    c.set_gram_mode(2)
+    S_tc, lam_tc = c.schmidt_entropy(x, cut=cut, spectrum=True)
+    n = 1 << min(l, L - l)
+    np.testing.assert_allclose(lam_tc, want[:n], atol=2e-6)
+    assert abs(S_tc - O.entropy_from_spectrum(want)) < 1e-5
+    c.set_gram_mode(1)
+    S_cc, lam_cc = c.schmidt_entropy(x, cut=cut, spectrum=True)
+    np.testing.assert_allclose(lam_tc, lam_cc, atol=2e-6)
+
+
+def test_tensor_core_gram_product_state_and_ghz():
+    L = 16
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec="mixed")
+    c.set_gram_mode(2)
+    x = c.new_state()
+    c.init_basis_state(x, si.neel_index(L))
+    S, lam = c.schmidt_entropy(x, spectrum=True)
+    assert abs(S) < 1e-6 and abs(lam[0] - 1.0) < 1e-6
+    g = to_dev(si.ghz_state(L), "mixed")
+    S, lam = c.schmidt_entropy(g, spectrum=True)
+    assert abs(S - math.log(2.0)) < 1e-6
+    np.testing.assert_allclose(lam[:2], 0.5, atol=1e-7)
