@@ -12,7 +12,9 @@
 //           the row and column blocks, 3-stage ring) and TMEM allocator;
 //   warp 1  one thread issues tcgen05.mma (cta_group::1, kind::tf32,
 //           M = N = 128, K = 8) and returns stages with tcgen05.commit;
-//   all 4 warps read the FP32 accumulator back with tcgen05.ld.
+//   warps 2..5 read each K-chunk's FP32 accumulator back with tcgen05.ld
+//           and add it into registers (the tensor cores' accumulation
+//           truncates; chunking keeps that bias near 2^-24 x 48).
 // Only the tiles of the upper triangle (row block <= column block) of Re rho
 // are formed: that is the triangle the eigenvalue solver reads.  All waits are
 // bounded; on timeout the kernel raises the error flag, lets the MMAs it
@@ -31,7 +33,8 @@ constexpr int kKc = 32;                    // floats per stage row (128 bytes)
 constexpr int kStages = 3;
 constexpr int kOpBytes = kTile * kKc * 4;  // one operand tile: 16 KiB
 constexpr int kStageBytes = 4 * kOpBytes;  // A_hi, A_lo, B_hi, B_lo
-constexpr int kThreads = 128;
+constexpr int kThreads = 192;                // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kChunk = 4;                    // stages accumulated in TMEM before a register readout
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned su(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -124,6 +127,11 @@ __global__ void split_planes_kernel(const float2 *psi, int n, long long K, float
 
 // One 128 x 128 tile of  mode 0: Re rho = P P^T (upper-triangle tiles)
 //                        mode 1: G = P[:, :K] P[:, K:]^T (all tiles)
+// The tensor cores accumulate in FP32 with truncation, so a long K-loop into
+// one TMEM accumulator is biased low (about 2^-24 per accumulation).  The
+// K-loop is therefore cut into chunks of kChunk stages, each accumulated in
+// one of two TMEM buffers and added by the epilogue warps into FP32 registers
+// (round to nearest) while the next chunk is computed.
 __global__ void __launch_bounds__(kThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap thi, const __grid_constant__ CUtensorMap tlo, int mode,
                    int n, int K, float2 *rho, float *G, int *err) {
@@ -133,8 +141,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kStages * kStageBytes);
     unsigned long long *empty = full + kStages;
-    unsigned long long *done = empty + kStages;
-    unsigned *tmem_slot = reinterpret_cast<unsigned *>(done + 1);
+    unsigned long long *chunk_done = empty + kStages;  // [2]
+    unsigned long long *acc_free = chunk_done + 2;     // [2]
+    unsigned long long *drain = acc_free + 2;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(drain + 1);
 
     const int T = n / kTile;
     int ty, tx;
@@ -158,12 +168,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             bar_init(&full[s], 1);
             bar_init(&empty[s], 1);
         }
-        bar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&chunk_done[b], 1);
+            bar_init(&acc_free[b], 4);
+        }
+        bar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su(tmem_slot)),
-                     "r"(kTile)
+                     "r"(2 * kTile)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -173,92 +187,120 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned tmem = *tmem_slot;
 
     const int nk = (mode == 0 ? 2 * K : K) / kKc;
+    const int nchunks = (nk + kChunk - 1) / kChunk;
     const int kb = (mode == 0) ? 0 : K;
 
-    if (warp == 0 && lane == 0) {
-        // ---- TMA producer ----
-        int issued = 0;
-        for (int s = 0; s < nk; ++s) {
-            const int st = s % kStages;
-            if (s >= kStages && !wait_bounded(&empty[st], (unsigned)(((s / kStages) - 1) & 1), err)) {
-                atomicExch(err, 1);
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            int issued = 0;
+            for (int s = 0; s < nk; ++s) {
+                const int st = s % kStages;
+                if (s >= kStages && !wait_bounded(&empty[st], (unsigned)(((s / kStages) - 1) & 1), err)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                unsigned char *base = smem + st * kStageBytes;
+                bar_expect_tx(&full[st], kStageBytes);
+                tma2d(base, &thi, s * kKc, x0, &full[st]);
+                tma2d(base + kOpBytes, &tlo, s * kKc, x0, &full[st]);
+                tma2d(base + 2 * kOpBytes, &thi, kb + s * kKc, y0, &full[st]);
+                tma2d(base + 3 * kOpBytes, &tlo, kb + s * kKc, y0, &full[st]);
+                ++issued;
             }
-            unsigned char *base = smem + st * kStageBytes;
-            bar_expect_tx(&full[st], kStageBytes);
-            tma2d(base, &thi, s * kKc, x0, &full[st]);
-            tma2d(base + kOpBytes, &tlo, s * kKc, x0, &full[st]);
-            tma2d(base + 2 * kOpBytes, &thi, kb + s * kKc, y0, &full[st]);
-            tma2d(base + 3 * kOpBytes, &tlo, kb + s * kKc, y0, &full[st]);
-            ++issued;
+            // every copy issued has landed before the CTA moves on
+            for (int s = issued > kStages ? issued - kStages : 0; s < issued; ++s)
+                wait_bounded(&full[s % kStages], (unsigned)((s / kStages) & 1), err);
         }
-        // every copy issued has landed before the CTA moves on
-        for (int s = issued > kStages ? issued - kStages : 0; s < issued; ++s)
-            wait_bounded(&full[s % kStages], (unsigned)((s / kStages) & 1), err);
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer ----
-        for (int s = 0; s < nk; ++s) {
-            const int st = s % kStages;
-            if (!wait_bounded(&full[st], (unsigned)((s / kStages) & 1), err)) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            for (int s = 0; s < nk; ++s) {
+                const int st = s % kStages;
+                const int c = s / kChunk, buf = c & 1;
+                if (s % kChunk == 0 && c >= 2 &&
+                    !wait_bounded(&acc_free[buf], (unsigned)(((c / 2) - 1) & 1), err)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                if (!wait_bounded(&full[st], (unsigned)((s / kStages) & 1), err)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned base = su(smem + st * kStageBytes);
+                const unsigned dcol = tmem + (unsigned)(buf * kTile);
+#pragma unroll
+                for (int kk = 0; kk < kKc / 8; ++kk) {
+                    const unsigned off = kk * 32;  // 8 tf32 = 32 bytes along K
+                    const unsigned long long ahi = smem_desc(base + off), alo = smem_desc(base + kOpBytes + off);
+                    const unsigned long long bhi = smem_desc(base + 2 * kOpBytes + off);
+                    const unsigned long long blo = smem_desc(base + 3 * kOpBytes + off);
+                    mma_tf32(dcol, ahi, bhi, ((s % kChunk) | kk) != 0 ? 1u : 0u);
+                    mma_tf32(dcol, ahi, blo, 1u);
+                    mma_tf32(dcol, alo, bhi, 1u);
+                }
+                mma_commit(&empty[st]);  // stage free once these MMAs have read it
+                if (s % kChunk == kChunk - 1 || s == nk - 1) mma_commit(&chunk_done[buf]);
+            }
+            // no MMA of this CTA is in flight past this point
+            mma_commit(drain);
+            wait_bounded(drain, 0u, err);
+        }
+    } else {
+        // ---- epilogue warps: TMEM chunk -> FP32 registers ----
+        const int lg = warp & 3;  // TMEM lane group this warp may access
+        float sum[kTile];
+#pragma unroll
+        for (int j = 0; j < kTile; ++j) sum[j] = 0.0f;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1;
+            if (!wait_bounded(&chunk_done[buf], (unsigned)((c / 2) & 1), err)) {
                 atomicExch(err, 1);
+                ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned base = su(smem + st * kStageBytes);
 #pragma unroll
-            for (int kk = 0; kk < kKc / 8; ++kk) {
-                const unsigned off = kk * 32;  // 8 tf32 = 32 bytes along K
-                const unsigned long long ahi = smem_desc(base + off), alo = smem_desc(base + kOpBytes + off);
-                const unsigned long long bhi = smem_desc(base + 2 * kOpBytes + off);
-                const unsigned long long blo = smem_desc(base + 3 * kOpBytes + off);
-                mma_tf32(tmem, ahi, bhi, (s | kk) != 0 ? 1u : 0u);
-                mma_tf32(tmem, ahi, blo, 1u);
-                mma_tf32(tmem, alo, bhi, 1u);
+            for (int q = 0; q < kTile / 32; ++q) {
+                unsigned v[32];
+                const unsigned taddr = tmem + ((unsigned)(lg * 32) << 16) + (unsigned)(buf * kTile + q * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
+                    "%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) sum[q * 32 + j] += __uint_as_float(v[j]);
             }
-            mma_commit(&empty[st]);  // stage free once these MMAs have read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su(&acc_free[buf])) : "memory");
         }
-        mma_commit(done);  // arrives when every MMA issued above has completed
-    }
-    __syncwarp();
-
-    // ---- epilogue: TMEM -> registers -> global ----
-    const bool ok = wait_bounded(done, 0u, err);
-    if (!ok) atomicExch(err, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        const int row = warp * 32 + lane;
-#pragma unroll 1
-        for (int c = 0; c < kTile / 32; ++c) {
-            unsigned v[32];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(c * 32);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                "[%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const long long o = (long long)(x0 + row) * n + y0 + c * 32;
+        if (ok) {
+            const int row = lg * 32 + lane;
+            const long long o = (long long)(x0 + row) * n + y0;
             if (mode == 0) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) rho[o + j].x = __uint_as_float(v[j]);
+                for (int j = 0; j < kTile; ++j) rho[o + j].x = sum[j];
             } else {
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)
-                    *reinterpret_cast<float4 *>(&G[o + j]) =
-                        make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
-                                    __uint_as_float(v[j + 3]));
+                for (int j = 0; j < kTile; j += 4)
+                    *reinterpret_cast<float4 *>(&G[o + j]) = make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile) : "memory");
 }
 
 // Im rho[x][y] = G[y][x] - G[x][y] on the upper triangle (x <= y); 32 x 32
