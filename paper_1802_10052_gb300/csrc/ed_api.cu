@@ -233,6 +233,7 @@ void destroy_handle(Handle *h) {
     }
     dev_free(h, h->Ell, 0);
     dev_free(h, h->Fhh, 0);
+    dev_free(h, h->Tab, 0);
     dev_free(h, h->partials, 0);
     dev_free(h, h->partials2, 0);
     dev_free(h, h->dscratch, 0);

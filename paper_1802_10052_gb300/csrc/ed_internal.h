@@ -132,6 +132,7 @@ struct Handle {
     // tables for the diagonal energy
     void *Ell;                  // 2^a1 entries (T)
     void *Fhh;                  // 2^(L-a1) x (a1+1) entries (T)
+    void *Tab;                  // 2^(L-a1) x 192 entries (T): per-tile TA, TB
 
     // scratch
     double *partials;           // per-CTA partial sums

@@ -69,7 +69,7 @@ struct PassParams {
     const typename Cx<T>::v16 *stream;  // elementwise input: previous Lanczos vector (first pass) or partial sum
     typename Cx<T>::v16 *out;
     const T *Ell;
-    const T *Fhh;
+    const T *Tab;                       // per-tile diagonal tables: TA[64] then TB[128] (first pass)
     const double *epi;                  // sv, a, b (device) or null
     double *partials;                   // 4 doubles per consumer warp
     const int *m_eff;
@@ -192,6 +192,13 @@ __device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap *tm, int rank,
     }
 }
 
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 template <typename V>
 __device__ __forceinline__ void st_stream(V *ptr, const V &v) {
     __stcs(ptr, v);
@@ -246,8 +253,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            // first pass: the tile's copy and its diagonal tables are two arrivals
-            mbar_init(&fullU[s], p.first ? 2 : 1);
+            mbar_init(&fullU[s], 1);
             mbar_init(&emptyU[s], kConsumerWarps);
         }
         mbar_init(fullS, 1);
@@ -291,29 +297,11 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         if (lane == 0) {
             int crd[5];
             coords(t, crd);
-            mbar_arrive_expect_tx(&fullU[s], p.tile_bytes);
+            const unsigned tab_bytes = p.first ? (unsigned)(kTab * sizeof(T)) : 0u;
+            mbar_arrive_expect_tx(&fullU[s], p.tile_bytes + tab_bytes);
             tma_load(U + (size_t)s * kTileV, &tm_u, p.rank, crd, &fullU[s]);
-        }
-        if (p.first) {
-            // diagonal tables of tile t (built while its copy is in flight):
-            // TA[x] = E_hh + sum_{j<ta} s_j(x) F_j,  TB[y] = sum_j s_j(y) F_{ta+j}
-            const int a = p.g, ta = p.ta, tb = a - ta;
-            const T *F = p.Fhh + (size_t)t * (size_t)(a + 1);
-            T *tb_s = tab + s * kTab;
-            for (int x = lane; x < (1 << ta) + (1 << tb); x += 32) {
-                if (x < (1 << ta)) {
-                    T v = F[a];
-                    for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -F[j] : F[j];
-                    tb_s[x] = v;
-                } else {
-                    const int y = x - (1 << ta);
-                    T v = (T)0;
-                    for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -F[ta + j] : F[ta + j];
-                    tb_s[64 + y] = v;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&fullU[s]);  // second arrival: tables written
+            // first pass: the tile's diagonal tables (precomputed per tile) ride on the same barrier
+            if (p.first) bulk_load(tab + s * kTab, p.Tab + (size_t)t * kTab, tab_bytes, &fullU[s]);
         }
         return true;
     };
@@ -608,6 +596,30 @@ __global__ void fhh_table_kernel(T *Fhh, int L, int a1, const double *Jr, long l
     Fhh[idx] = (T)s;
 }
 
+// Per-tile tables of the first pass: TA[x] = E_hh + sum_{j<ta} s_j(x) F_j and
+// TB[y] = sum_{j<a1-ta} s_j(y) F_{ta+j} for every tile (row of Fhh).
+template <typename T>
+__global__ void tab_table_kernel(T *Tab, const T *Fhh, long long ntiles, int a1, int ta) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ntiles * kTab) return;
+    const long long t = idx / kTab;
+    const int x = (int)(idx % kTab);
+    const T *F = Fhh + (size_t)t * (size_t)(a1 + 1);
+    const int tb = a1 - ta;
+    double v = 0.0;
+    if (x < 64) {
+        if (x < (1 << ta)) {
+            v = (double)F[a1];
+            for (int j = 0; j < ta; ++j) v += ((x >> j) & 1) ? -(double)F[j] : (double)F[j];
+        }
+    } else {
+        const int y = x - 64;
+        if (y < (1 << tb))
+            for (int j = 0; j < tb; ++j) v += ((y >> j) & 1) ? -(double)F[ta + j] : (double)F[ta + j];
+    }
+    Tab[idx] = (T)v;
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -766,6 +778,16 @@ static cudaError_t build_tables_t(Handle *h) {
         fhh_table_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>((T *)h->Fhh, h->L, a1, Jd, nt);
         err = cudaGetLastError();
     }
+    if (err == cudaSuccess) {
+        h->Tab = dev_alloc(h, sizeof(T) * (size_t)nt * kTab, &err);
+        if (err == cudaSuccess) {
+            const long long n2 = nt * kTab;
+            tab_table_kernel<T><<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>((T *)h->Tab,
+                                                                                     (const T *)h->Fhh, nt, a1,
+                                                                                     h->plan.ta);
+            err = cudaGetLastError();
+        }
+    }
     cudaError_t e2 = cudaStreamSynchronize(h->stream);
     cudaFree(Jd);
     return err != cudaSuccess ? err : e2;
@@ -810,7 +832,7 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.stream = reinterpret_cast<const V *>(stream);
         p.out = reinterpret_cast<V *>(dst);
         p.Ell = reinterpret_cast<const T *>(h->Ell);
-        p.Fhh = reinterpret_cast<const T *>(h->Fhh);
+        p.Tab = reinterpret_cast<const T *>(h->Tab);
         p.epi = a.epi;
         p.partials = a.partials;
         p.m_eff = a.m_eff;
