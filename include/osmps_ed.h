@@ -9,7 +9,7 @@
  *
  * Model (arXiv:1802.10052, Eq. genericH with one site rule sigma^x and one
  * distance-only infinite-function rule sigma^z sigma^z; the nearest-neighbour
- * quantum Ising model Eq. HQI and the long-range H_LRQI of Sec. VI are special
+ * quantum Ising model Eq. HQI and the long-range H_LRQI of Sec. VII are special
  * cases):
  *
  *     H = sum_{i<j} J(j-i) sz_i sz_j + sum_k h_k sx_k        (signed inputs)
@@ -73,7 +73,7 @@ typedef enum {
 /*
  * Create a handle for a chain of L sites (1 <= L <= OSMPS_MAX_L).
  * Paper: Eq. genericH (site rule + infinite-function rule, coupling depending
- * only on the distance, c_{k',k} = c(k'-k)); Eq. HQI; H_LRQI (Sec. VI).
+ * only on the distance, c_{k',k} = c(k'-k)); Eq. HQI; H_LRQI (Sec. VII).
  *   couplings  host array J(r) for r = 1..L-1 (index r-1), or NULL.  When NULL,
  *              J(r) = J / r^alpha; alpha < 0 (or +inf) keeps only J(1) = J
  *              (nearest neighbours).
@@ -243,6 +243,53 @@ osmps_status osmps_ed_timing_read(osmps_ed_t *ed, double *hpsi_ms, int64_t *hpsi
 /* Number of kernels this handle has launched so far (its own kernels; the
  * cuSOLVER eigenvalue routine is not counted).  Not from the paper. */
 osmps_status osmps_ed_launch_count(const osmps_ed_t *ed, int64_t *count);
+
+/*
+ * Batched ground states: the lowest eigenpair of many independent chains in
+ * one persistent launch (statics, Sec. II, for a set of Hamiltonians of
+ * Eq. genericH).  Each CTA of the launch takes one chain at a time from a work
+ * queue (largest first) and runs that chain's Lanczos iteration by itself, so
+ * chains converge independently; no Krylov basis is stored (a second sweep
+ * regenerates the vectors to form the Ritz vector).  Vectors are complex64
+ * (OSMPS_MIXED) or complex128 (OSMPS_FP64); alpha, beta, all reductions and
+ * the tridiagonal problem are FP64.
+ *
+ * osmps_ed_batch_create: n chains; chain k has L[k] sites with
+ *   J(r) = J[k] / r^alpha[k] (alpha[k] < 0 or +inf: nearest neighbour only,
+ *   J(1) = J[k]) and uniform field h[k].  L[k] must lie in [13, 22] for
+ *   OSMPS_MIXED and [12, 22] for OSMPS_FP64 (one 64 KiB tile of low bits).
+ *   max_iter (1..1000) bounds the Lanczos steps per chain.  Allocates every
+ *   buffer the solve needs (four packed vectors and per-CTA scratch).
+ * osmps_ed_batch_offsets: host array of n + 1 amplitude offsets; chain k's
+ *   state occupies [offsets[k], offsets[k+1]) of the packed state buffer
+ *   (each offset a multiple of 32 amplitudes; offsets[n] is the total).
+ * osmps_ed_batch_lanczos_ground: psi (device, packed, offsets as above) holds
+ *   the start vectors on entry (any non-zero vectors) and the normalised
+ *   ground states on return.  energy, residual (doubles), iters and status
+ *   (ints) are DEVICE arrays of n entries: the lowest Ritz value, the true
+ *   residual |H x - theta x| of the returned state, the Lanczos steps taken,
+ *   and the chain's osmps_status (OSMPS_ENOCONV when max_iter steps did not
+ *   bring beta_{j+1} |y_j| below tol; the best Ritz pair is still returned).
+ *   The call only enqueues work on the handle's stream (a memset and one
+ *   kernel launch; with osmps_ed_batch_set_graph(b, 1) one CUDA graph launch)
+ *   and allocates nothing, so it may itself be captured into a CUDA graph.
+ * osmps_ed_batch_check: synchronises the stream; OSMPS_ETIMEOUT if a bounded
+ *   device wait of the last solve gave up (chains then carry OSMPS_ETIMEOUT).
+ */
+typedef struct osmps_ed_batch osmps_ed_batch_t;
+osmps_status osmps_ed_batch_create(int n, const int *L, const double *J, const double *alpha, const double *h,
+                                   int prec, int max_iter, void *cuda_stream, osmps_ed_batch_t **out);
+osmps_status osmps_ed_batch_destroy(osmps_ed_batch_t *b);
+osmps_status osmps_ed_batch_offsets(const osmps_ed_batch_t *b, uint64_t *offsets);
+osmps_status osmps_ed_batch_device_bytes(const osmps_ed_batch_t *b, uint64_t *bytes);
+osmps_status osmps_ed_batch_set_graph(osmps_ed_batch_t *b, int enable);
+/* CTAs of the persistent launch (0 = one per SM, the default; at most one
+ * CTA fits on an SM).  A tuning knob, not from the paper. */
+osmps_status osmps_ed_batch_set_grid(osmps_ed_batch_t *b, int ctas);
+osmps_status osmps_ed_batch_lanczos_ground(osmps_ed_batch_t *b, void *psi, double tol, double *energy,
+                                           double *residual, int *iters, int *status);
+osmps_status osmps_ed_batch_check(osmps_ed_batch_t *b);
+osmps_status osmps_ed_batch_launch_count(const osmps_ed_batch_t *b, int64_t *count);
 
 /* Static description of a status code. */
 const char *osmps_ed_strerror(osmps_status status);

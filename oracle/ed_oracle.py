@@ -20,7 +20,7 @@ Everything here is deliberately slow and obvious, in float64 / complex128:
   entropy through rho = M M^dagger (Sec. IV, bond entropy).
 
 Model (Eq. genericH restricted to one site rule and one distance-only
-infinite-function rule; Eq. HQI and the long-range H_LRQI of Sec. VI are the
+infinite-function rule; Eq. HQI and the long-range H_LRQI of Sec. VII are the
 special cases J(r) = -delta_{r,1}, h -> -h and J(r) = -cos(phi)/r^alpha,
 h = -sin(phi)):
 
@@ -204,6 +204,20 @@ def jordan_wigner_ground_energy(L: int, J: float, h: float) -> float:
     """
     B = np.diag(np.full(L, abs(h))) + np.diag(np.full(L - 1, abs(J)), 1)
     return -float(np.sum(np.linalg.svd(B, compute_uv=False)))
+
+
+def ground_energy_sparse(L: int, Jr: np.ndarray, h) -> float:
+    """Lowest eigenvalue of the CSR Hamiltonian by ARPACK (scipy eigsh, the
+    routine the paper uses for statics, Sec. II): the plain definition of the
+    ground energy for chains too long for dense eigh."""
+    from scipy.sparse.linalg import eigsh
+
+    H = hamiltonian_csr(L, Jr, h)
+    # a generic start vector: a symmetric one (e.g. all ones) stays inside one
+    # parity / reflection sector and can miss the ground state
+    v0 = np.random.Generator(np.random.Philox(20180227)).standard_normal(H.shape[0])
+    vals = eigsh(H, k=1, which="SA", tol=1e-13, v0=v0, return_eigenvectors=False)
+    return float(vals[0])
 
 
 # ---------------------------------------------------------------------------

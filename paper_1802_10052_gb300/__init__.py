@@ -20,7 +20,7 @@ import numpy as np
 
 from ._binding import (LIB_PATH, OSMPS_ENOCONV, OSMPS_FP64, OSMPS_MIXED, OSMPS_OK, OsmpsError, check, lib)
 
-__all__ = ["Chain", "OsmpsError", "LIB_PATH", "lib"]
+__all__ = ["Chain", "ChainBatch", "OsmpsError", "LIB_PATH", "lib"]
 
 _PREC = {"fp64": OSMPS_FP64, "mixed": OSMPS_MIXED}
 
@@ -203,3 +203,100 @@ class Chain:
         lp = lam.ctypes.data_as(C.POINTER(C.c_double)) if spectrum else None
         check(lib.osmps_ed_schmidt_entropy(self._h, _dptr(psi), int(c), lp, C.byref(S)), "osmps_ed_schmidt_entropy")
         return (S.value, lam) if spectrum else S.value
+
+
+class ChainBatch:
+    """Ground states of many independent chains in one persistent launch.
+
+    Chain k: H_k = sum_{i<j} J[k]/|i-j|^alpha[k] sz_i sz_j + h[k] sum_i sx_i on L[k]
+    sites (``alpha[k]`` None: nearest neighbours only).  States are packed in
+    one tensor; chain k occupies ``psi[offsets[k]:offsets[k+1]]``.
+    """
+
+    def __init__(self, L, J, alpha, h, prec="mixed", max_iter=1000, stream=None):
+        torch = _torch()
+        n = len(L)
+        self.n = n
+        self.L = [int(x) for x in L]
+        self.prec = prec
+        self.dtype = torch.complex128 if prec == "fp64" else torch.complex64
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        Ja = (C.c_double * n)(*[float(x) for x in J])
+        Aa = (C.c_double * n)(*[-1.0 if a is None else float(a) for a in alpha])
+        Ha = (C.c_double * n)(*[float(x) for x in h])
+        La = (C.c_int * n)(*self.L)
+        handle = C.c_void_p()
+        check(lib.osmps_ed_batch_create(n, La, Ja, Aa, Ha, _PREC[prec], int(max_iter),
+                                        C.c_void_p(self._stream.cuda_stream), C.byref(handle)),
+              "osmps_ed_batch_create")
+        self._h = handle
+        off = (C.c_uint64 * (n + 1))()
+        check(lib.osmps_ed_batch_offsets(self._h, off), "osmps_ed_batch_offsets")
+        self.offsets = np.array(off[:], dtype=np.int64)
+        self.energy = torch.zeros(n, dtype=torch.float64, device="cuda")
+        self.residual = torch.zeros(n, dtype=torch.float64, device="cuda")
+        self.iters = torch.zeros(n, dtype=torch.int32, device="cuda")
+        self.status = torch.zeros(n, dtype=torch.int32, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.osmps_ed_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def total(self):
+        return int(self.offsets[-1])
+
+    def new_states(self):
+        torch = _torch()
+        return torch.empty(self.total, dtype=self.dtype, device="cuda")
+
+    def view(self, psi, k):
+        return psi[int(self.offsets[k]):int(self.offsets[k + 1])]
+
+    def device_bytes(self):
+        v = C.c_uint64()
+        check(lib.osmps_ed_batch_device_bytes(self._h, C.byref(v)), "osmps_ed_batch_device_bytes")
+        return v.value
+
+    def set_graph(self, on=True):
+        check(lib.osmps_ed_batch_set_graph(self._h, 1 if on else 0), "osmps_ed_batch_set_graph")
+
+    def set_grid(self, ctas):
+        check(lib.osmps_ed_batch_set_grid(self._h, int(ctas)), "osmps_ed_batch_set_grid")
+
+    def launch_count(self):
+        v = C.c_int64()
+        check(lib.osmps_ed_batch_launch_count(self._h, C.byref(v)), "osmps_ed_batch_launch_count")
+        return v.value
+
+    def lanczos_ground_async(self, psi, tol=1e-10):
+        """Enqueue the solve (start vectors in, ground states out); results land in
+        the device tensors ``energy``, ``residual``, ``iters``, ``status``."""
+        if psi.dtype != self.dtype or not psi.is_cuda or psi.numel() != self.total:
+            raise ValueError("psi must be a packed CUDA state tensor of this batch")
+        check(lib.osmps_ed_batch_lanczos_ground(self._h, _dptr(psi), float(tol), _dptr(self.energy),
+                                                _dptr(self.residual), _dptr(self.iters), _dptr(self.status)),
+              "osmps_ed_batch_lanczos_ground")
+
+    def check(self):
+        check(lib.osmps_ed_batch_check(self._h), "osmps_ed_batch_check")
+
+    def lanczos_ground(self, psi, tol=1e-10):
+        """Solve and return host arrays (energy, residual, iters, status)."""
+        self.lanczos_ground_async(psi, tol)
+        self.check()
+        return (self.energy.cpu().numpy(), self.residual.cpu().numpy(), self.iters.cpu().numpy(),
+                self.status.cpu().numpy())

@@ -47,6 +47,15 @@ SIGNATURES = {
     "osmps_ed_launch_count": (_I, [_P, C.POINTER(C.c_int64)]),
     "osmps_ed_timing_enable": (_I, [_P, _I]),
     "osmps_ed_timing_read": (_I, [_P, _DP, C.POINTER(C.c_int64), _I]),
+    "osmps_ed_batch_create": (_I, [_I, C.POINTER(_I), _DP, _DP, _DP, _I, _I, _P, C.POINTER(_P)]),
+    "osmps_ed_batch_destroy": (_I, [_P]),
+    "osmps_ed_batch_offsets": (_I, [_P, C.POINTER(_U64)]),
+    "osmps_ed_batch_device_bytes": (_I, [_P, C.POINTER(_U64)]),
+    "osmps_ed_batch_set_graph": (_I, [_P, _I]),
+    "osmps_ed_batch_set_grid": (_I, [_P, _I]),
+    "osmps_ed_batch_lanczos_ground": (_I, [_P, _P, _D, _P, _P, _P, _P]),
+    "osmps_ed_batch_check": (_I, [_P]),
+    "osmps_ed_batch_launch_count": (_I, [_P, C.POINTER(C.c_int64)]),
     "osmps_ed_strerror": (C.c_char_p, [_I]),
 }
 

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libosmps_ed.so")
-SOURCES = ["ed_api.cu", "hpsi_kernels.cu", "vec_kernels.cu", "measure_kernels.cu", "gram_tc.cu"]
+SOURCES = ["ed_api.cu", "hpsi_kernels.cu", "vec_kernels.cu", "measure_kernels.cu", "gram_tc.cu", "batch_kernels.cu",
+           "batch_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +40,7 @@ def common_flags(extra=()):
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
     return files

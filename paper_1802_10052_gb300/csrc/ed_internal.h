@@ -171,4 +171,55 @@ struct Handle {
 void *dev_alloc(Handle *h, size_t bytes, cudaError_t *err);
 void dev_free(Handle *h, void *p, size_t bytes);
 
+// ---------------------------------------------------------------------------
+// Batched ground states (batch_kernels.cu, batch_api.cu)
+// ---------------------------------------------------------------------------
+constexpr int kBatchMaxL = 22;          // gathered pass-B segments stay >= 64 bytes
+constexpr int kBatchEllScratch = 4096;  // doubles per CTA for the E_ll table of the 64 KiB tile
+
+// One chain of a batch as the kernel sees it.
+struct BatchInst {
+    long long off;                      // amplitude offset of its state in the packed buffers
+    int L;
+    int pad;
+    double h;                           // uniform transverse field
+    double J[kMaxL + 1];                // J(r), r = 1..L-1 (J[0] = 0)
+};
+
+struct BatchHandle {
+    int device;
+    int nsm;
+    int n;
+    int prec;
+    int max_iter;
+    int grid;                           // CTAs of the persistent launch
+    cudaStream_t stream;
+    long long total;                    // packed state length (amplitudes)
+    long long *offsets;                 // host, n + 1
+    BatchInst *d_inst;
+    int *d_order;                       // chain order of the work queue (largest first)
+    void *R[3];                         // recurrence vectors (packed like the states)
+    void *X;                            // Ritz vector accumulator
+    double *scratch;                    // per CTA: alpha, beta, y, tridiagonal work
+    int *counter;                       // work-queue head
+    int *err;                           // raised when a bounded wait gives up
+    uint64_t owned_bytes;
+    uint64_t launches;
+    // CUDA graph of one solve, captured on first use with a given argument set
+    int use_graph;
+    cudaGraphExec_t graph;
+    void *g_psi;
+    double g_tol;
+    double *g_energy, *g_residual;
+    int *g_iters, *g_status;
+};
+
+namespace batch {
+size_t batch_smem_bytes(int prec);
+int batch_tile_bits(int prec);
+cudaError_t batch_prepare(int prec);
+cudaError_t launch_batch(BatchHandle *b, void *psi, double tol, double *energy, double *residual, int *iters,
+                         int *status);
+}  // namespace batch
+
 }  // namespace osmps

@@ -72,6 +72,22 @@ def batched_instances(n: int = 512, seed: int = 3, lmin: int = 14, lmax: int = 2
     return [(int(a), float(b), float(c)) for a, b, c in zip(Ls, alphas, hs)]
 
 
+def batch_start_states(Ls, seed: int = 3, dtype=np.complex128):
+    """Seeded complex Gaussian start vectors of a batch, one Philox stream per chain.
+
+    Chain k draws from the Philox-4x32-10 generator with key ``seed`` jumped k
+    times (disjoint streams); Re and Im iid N(0,1), normalised to 1.
+    """
+    base = np.random.Philox(seed)
+    out = []
+    for k, L in enumerate(Ls):
+        rng = np.random.Generator(base.jumped(k))
+        v = rng.standard_normal(2 << int(L)).view(np.complex128)
+        v /= np.linalg.norm(v)
+        out.append(v.astype(dtype))
+    return out
+
+
 def field_schedule(nsteps: int = 200, seed: int = 4, lo: float = 0.5, hi: float = 1.5) -> np.ndarray:
     """Seeded piecewise-constant field values h_k ~ U[lo, hi], one per time step."""
     rng = np.random.Generator(np.random.Philox(seed))

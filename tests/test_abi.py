@@ -60,3 +60,33 @@ def test_strerror_and_host_side_argument_checks():
     assert lib.osmps_ed_destroy(None) == B.OSMPS_OK
     assert lib.osmps_ed_apply_H(None, None, None) == B.OSMPS_EINVAL
     assert lib.osmps_ed_krylov_evolve(None, None, 0.1, 1, 20, 0.0, None) == B.OSMPS_EINVAL
+
+
+def test_batch_host_side_argument_checks():
+    """osmps_ed_batch_create rejects bad arguments before touching CUDA."""
+    from paper_1802_10052_gb300 import _binding as B
+    lib = B.lib
+    h = C.c_void_p()
+
+    def create(Ls, prec=B.OSMPS_MIXED, max_iter=100, hval=1.0, out=True):
+        n = len(Ls)
+        La = (C.c_int * max(n, 1))(*Ls)
+        one = (C.c_double * max(n, 1))(*([1.0] * max(n, 1)))
+        hh = (C.c_double * max(n, 1))(*([hval] * max(n, 1)))
+        return lib.osmps_ed_batch_create(n, La, one, one, hh, prec, max_iter, None, C.byref(h) if out else None)
+
+    assert create([14], out=False) == B.OSMPS_EINVAL
+    assert create([]) == B.OSMPS_EINVAL
+    assert create([0]) == B.OSMPS_EINVAL
+    assert create([31]) == B.OSMPS_EINVAL
+    assert create([14], prec=5) == B.OSMPS_EINVAL
+    assert create([14], max_iter=0) == B.OSMPS_EINVAL
+    assert create([14], max_iter=1001) == B.OSMPS_EINVAL
+    assert create([14], hval=float("nan")) == B.OSMPS_EINVAL
+    # valid chains outside the tile range of the batched solver
+    assert create([12]) == B.OSMPS_EUNSUPPORTED
+    assert create([11], prec=B.OSMPS_FP64) == B.OSMPS_EUNSUPPORTED
+    assert create([14, 23]) == B.OSMPS_EUNSUPPORTED
+    assert lib.osmps_ed_batch_destroy(None) == B.OSMPS_EINVAL
+    assert lib.osmps_ed_batch_lanczos_ground(None, None, 1e-10, None, None, None, None) == B.OSMPS_EINVAL
+    assert lib.osmps_ed_batch_check(None) == B.OSMPS_EINVAL

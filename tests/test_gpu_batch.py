@@ -1,0 +1,124 @@
+"""Batched Lanczos ground states (many chains, one persistent launch) through
+the C ABI against the FP64 oracle: energies against ARPACK on the oracle's CSR
+matrix and the Jordan-Wigner closed form, returned states checked by the
+oracle's own product, bit-identical reruns and CUDA-graph replays."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import seeded_inputs as si
+from oracle import ed_oracle as O
+from _gpu import TOL
+
+pytestmark = pytest.mark.gpu
+
+# true-residual bounds |H x - E x| / max(1, |E|) of the returned states: the
+# complex64 vectors carry ~1e-7 relative rounding per amplitude
+RES_TOL = {"fp64": 1e-8, "mixed": 5e-5}
+
+
+def ChainBatch(*a, **k):
+    from paper_1802_10052_gb300 import ChainBatch as _B
+    return _B(*a, **k)
+
+
+def pack(vecs, prec):
+    dt = np.complex64 if prec == "mixed" else np.complex128
+    return torch.from_numpy(np.concatenate([v.astype(dt) for v in vecs])).cuda()
+
+
+def small_set(prec, n=10, seed=11):
+    lo = 13 if prec == "mixed" else 12
+    rng = np.random.Generator(np.random.Philox(seed))
+    Ls = [int(x) for x in rng.integers(lo, lo + 3, size=n)]
+    alphas = [None if k == 0 else float(a) for k, a in enumerate(rng.uniform(0.5, 3.0, size=n))]
+    hs = [float(x) for x in rng.uniform(0.2, 2.0, size=n)]
+    return Ls, alphas, hs
+
+
+def check_chain(b, psi, k, L, alpha, h, E, R, prec):
+    E0 = O.ground_energy_sparse(L, O.coupling_table(L, 1.0, alpha), h)
+    assert abs(E[k] - E0) <= TOL[prec] * max(1.0, abs(E0)), (k, L, E[k], E0)
+    x = b.view(psi, k).cpu().numpy().astype(np.complex128)
+    assert abs(np.linalg.norm(x) - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
+    H = O.hamiltonian_csr(L, O.coupling_table(L, 1.0, alpha), h)
+    r = float(np.linalg.norm(H @ x - E0 * x))
+    assert r <= RES_TOL[prec] * max(1.0, abs(E0)), (k, L, r)
+    # the reported residual is the same quantity (up to E vs E0 and rounding)
+    assert abs(R[k] - r) <= RES_TOL[prec] * max(1.0, abs(E0))
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_matches_oracle(prec):
+    Ls, alphas, hs = small_set(prec)
+    b = ChainBatch(Ls, [1.0] * len(Ls), alphas, hs, prec=prec, max_iter=800)
+    psi = pack(si.batch_start_states(Ls, seed=3), prec)
+    E, R, it, st = b.lanczos_ground(psi, tol=1e-10)
+    for k in range(len(Ls)):
+        print(f"chain {k}: L={Ls[k]} E={E[k]:.12f} res={R[k]:.2e} iters={it[k]} status={st[k]}")
+    assert (st == 0).all(), st
+    assert (it >= 2).all() and (it <= 800).all()
+    for k in range(len(Ls)):
+        check_chain(b, psi, k, Ls[k], alphas[k], hs[k], E, R, prec)
+    assert b.launch_count() == 1
+    b.close()
+
+
+def test_batch_nn_chains_against_free_fermions():
+    Ls, hs = [13, 14, 16], [0.5, 1.0, 1.5]
+    b = ChainBatch(Ls, [1.0] * 3, [None] * 3, hs, prec="mixed", max_iter=800)
+    psi = pack(si.batch_start_states(Ls, seed=5), "mixed")
+    E, R, it, st = b.lanczos_ground(psi, tol=1e-10)
+    assert (st == 0).all()
+    for k in range(3):
+        Ejw = O.jordan_wigner_ground_energy(Ls[k], 1.0, hs[k])
+        assert abs(E[k] - Ejw) <= 1e-5 * abs(Ejw)
+    b.close()
+
+
+def test_batch_rerun_and_graph_replay_are_bit_identical():
+    Ls, alphas, hs = small_set("mixed", n=6, seed=17)
+    b = ChainBatch(Ls, [1.0] * len(Ls), alphas, hs, prec="mixed", max_iter=600)
+    start = pack(si.batch_start_states(Ls, seed=9), "mixed")
+    psi1 = start.clone()
+    E1, R1, it1, st1 = b.lanczos_ground(psi1, tol=1e-10)
+    b.set_graph(True)
+    # the first call captures the graph, the second replays it (same buffers)
+    psi2 = start.clone()
+    E2, R2, it2, st2 = b.lanczos_ground(psi2, tol=1e-10)
+    psi2.copy_(start)
+    E3, R3, it3, st3 = b.lanczos_ground(psi2, tol=1e-10)
+    assert np.array_equal(E1, E2) and np.array_equal(E1, E3)
+    assert np.array_equal(it1, it2) and np.array_equal(it1, it3)
+    assert torch.equal(psi1, psi2)
+    assert b.launch_count() == 3
+    b.close()
+
+
+def test_batch_full_size_512_chains():
+    """512 long-range chains, L ~ U{14..20}, alpha ~ U[0.5, 3], h ~ U[0.2, 2],
+    each Lanczos to 1e-10 in one persistent launch (complex64 vectors, FP64
+    reductions).  Every chain: status, iteration count, residual; a sample of
+    chains of every length against the oracle."""
+    inst = si.batched_instances(512, seed=3)
+    Ls = [x[0] for x in inst]
+    alphas = [x[1] for x in inst]
+    hs = [x[2] for x in inst]
+    b = ChainBatch(Ls, [1.0] * 512, alphas, hs, prec="mixed", max_iter=1000)
+    psi = pack(si.batch_start_states(Ls, seed=3), "mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, R, it, st = b.lanczos_ground(psi, tol=1e-10)
+    dt = time.perf_counter() - t0
+    print(f"512 chains: {dt * 1e3:.1f} ms, iterations {it.min()}..{it.max()} (mean {it.mean():.1f})")
+    assert (st == 0).all(), np.unique(st, return_counts=True)
+    assert np.all(R <= RES_TOL["mixed"] * np.maximum(1.0, np.abs(E)))
+    norms = torch.stack([torch.linalg.vector_norm(b.view(psi, k)) for k in range(512)]).cpu().numpy()
+    assert np.all(np.abs(norms - 1.0) < 1e-5)
+    # oracle sample: the first chain of each length up to 18
+    for L in range(14, 19):
+        k = Ls.index(L)
+        check_chain(b, psi, k, L, alphas[k], hs[k], E, R, "mixed")
+    b.close()

@@ -293,3 +293,24 @@ def test_trace_distance_and_rate_helpers():
     r2 = np.diag([0.0, 1.0])
     assert abs(O.trace_distance(r1, r2) - 1.0) < 1e-15
     assert abs(O.convergence_rate(1e-2, 1e-4, 10.0) - 2.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# ground_energy_sparse (reference energies of the batched ground states)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,alpha,h", [(8, 0.5, 0.2), (9, 2.5, 1.8), (10, 1.3, 0.7)])
+def test_sparse_ground_energy_matches_dense_eigh(L, alpha, h):
+    """eigsh on the entry-by-entry CSR matrix against dense eigh of the
+    Kronecker-product Hamiltonian (two independent constructions)."""
+    Jr = O.coupling_table(L, 1.0, alpha)
+    E_dense = float(np.linalg.eigvalsh(O.hamiltonian_dense(L, Jr, h))[0])
+    assert abs(O.ground_energy_sparse(L, Jr, h) - E_dense) < 1e-11 * max(1.0, abs(E_dense))
+
+
+@pytest.mark.parametrize("L,h", [(13, 1.0), (14, 0.4)])
+def test_sparse_ground_energy_matches_jordan_wigner(L, h):
+    """Nearest-neighbour chains beyond dense size: the free-fermion closed form."""
+    Jr = O.coupling_table(L, 1.0, None)
+    E_jw = O.jordan_wigner_ground_energy(L, 1.0, h)
+    assert abs(O.ground_energy_sparse(L, Jr, h) - E_jw) < 1e-11 * abs(E_jw)
