@@ -283,9 +283,23 @@ osmps_status osmps_ed_batch_destroy(osmps_ed_batch_t *b);
 osmps_status osmps_ed_batch_offsets(const osmps_ed_batch_t *b, uint64_t *offsets);
 osmps_status osmps_ed_batch_device_bytes(const osmps_ed_batch_t *b, uint64_t *bytes);
 osmps_status osmps_ed_batch_set_graph(osmps_ed_batch_t *b, int enable);
-/* CTAs of the persistent launch (0 = one per SM, the default; at most one
- * CTA fits on an SM).  A tuning knob, not from the paper. */
-osmps_status osmps_ed_batch_set_grid(osmps_ed_batch_t *b, int ctas);
+/*
+ * Work split (a tuning knob, not from the paper).  csize = 1 (the default):
+ * every CTA solves one chain at a time.  csize = 2, 4 or 8: the launch uses
+ * thread-block clusters of csize CTAs; the chains with L >= lsplit are solved
+ * first, each by a whole cluster (tiles and vector ranges split over its CTAs,
+ * reductions through distributed shared memory), then the others one per CTA,
+ * so that a few long chains do not leave one SM working alone at the end.
+ * lsplit must satisfy lsplit >= 11 + log2(csize) (+1 for OSMPS_MIXED) and
+ * lsplit <= 22.  EUNSUPPORTED if no cluster of that size fits.
+ * osmps_ed_batch_autotune times one solve per candidate (csize 1; csize 2, 4,
+ * 8 with lsplit = Lmax-2 .. Lmax) on the given start vectors, keeps the
+ * fastest split and restores psi to the start vectors; best_ms (may be NULL)
+ * receives its device time.  It allocates a copy of psi and synchronises.
+ */
+osmps_status osmps_ed_batch_set_split(osmps_ed_batch_t *b, int csize, int lsplit);
+osmps_status osmps_ed_batch_get_split(const osmps_ed_batch_t *b, int *csize, int *lsplit, int *grid);
+osmps_status osmps_ed_batch_autotune(osmps_ed_batch_t *b, void *psi, double tol, double *best_ms);
 osmps_status osmps_ed_batch_lanczos_ground(osmps_ed_batch_t *b, void *psi, double tol, double *energy,
                                            double *residual, int *iters, int *status);
 osmps_status osmps_ed_batch_check(osmps_ed_batch_t *b);

@@ -274,8 +274,21 @@ class ChainBatch:
     def set_graph(self, on=True):
         check(lib.osmps_ed_batch_set_graph(self._h, 1 if on else 0), "osmps_ed_batch_set_graph")
 
-    def set_grid(self, ctas):
-        check(lib.osmps_ed_batch_set_grid(self._h, int(ctas)), "osmps_ed_batch_set_grid")
+    def set_split(self, csize, lsplit=22):
+        """Clusters of ``csize`` CTAs solve the chains with L >= ``lsplit`` (csize 1: none)."""
+        check(lib.osmps_ed_batch_set_split(self._h, int(csize), int(lsplit)), "osmps_ed_batch_set_split")
+
+    def get_split(self):
+        cs, ls, gr = C.c_int(), C.c_int(), C.c_int()
+        check(lib.osmps_ed_batch_get_split(self._h, C.byref(cs), C.byref(ls), C.byref(gr)), "osmps_ed_batch_get_split")
+        return cs.value, ls.value, gr.value
+
+    def autotune(self, psi, tol=1e-10):
+        """Time the candidate work splits on these start vectors (psi is restored) and
+        keep the fastest; returns (csize, lsplit, grid, best_ms)."""
+        ms = C.c_double()
+        check(lib.osmps_ed_batch_autotune(self._h, _dptr(psi), float(tol), C.byref(ms)), "osmps_ed_batch_autotune")
+        return self.get_split() + (ms.value,)
 
     def launch_count(self):
         v = C.c_int64()

@@ -52,7 +52,9 @@ SIGNATURES = {
     "osmps_ed_batch_offsets": (_I, [_P, C.POINTER(_U64)]),
     "osmps_ed_batch_device_bytes": (_I, [_P, C.POINTER(_U64)]),
     "osmps_ed_batch_set_graph": (_I, [_P, _I]),
-    "osmps_ed_batch_set_grid": (_I, [_P, _I]),
+    "osmps_ed_batch_set_split": (_I, [_P, _I, _I]),
+    "osmps_ed_batch_get_split": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "osmps_ed_batch_autotune": (_I, [_P, _P, _D, _DP]),
     "osmps_ed_batch_lanczos_ground": (_I, [_P, _P, _D, _P, _P, _P, _P]),
     "osmps_ed_batch_check": (_I, [_P]),
     "osmps_ed_batch_launch_count": (_I, [_P, C.POINTER(C.c_int64)]),

@@ -45,6 +45,8 @@ void release(BatchHandle *b) {
         if (p != nullptr) cudaFree(p);
     delete[] b->offsets;
     b->offsets = nullptr;
+    delete[] b->L;
+    b->L = nullptr;
 }
 
 // The launch of one solve (memset of the queue head + one kernel) captured
@@ -126,12 +128,22 @@ osmps_status osmps_ed_batch_create(int n, const int *L, const double *J, const d
         return from_cuda(err);
     }
     b->grid = std::min(n, b->nsm);
+    b->csize = 1;
+    b->lsplit = kBatchMaxL + 1;
+    b->nbig = 0;
 
     b->offsets = new (std::nothrow) long long[n + 1];
     if (b->offsets == nullptr) {
         delete ob;
         return OSMPS_ENOMEM;
     }
+    b->L = new (std::nothrow) int[n];
+    if (b->L == nullptr) {
+        delete[] b->offsets;
+        delete ob;
+        return OSMPS_ENOMEM;
+    }
+    std::copy(L, L + n, b->L);
     std::vector<BatchInst> inst(n);
     b->offsets[0] = 0;
     for (int k = 0; k < n; ++k) {
@@ -158,14 +170,14 @@ osmps_status osmps_ed_batch_create(int n, const int *L, const double *J, const d
     if (err == cudaSuccess)
         b->scratch = static_cast<double *>(balloc(b, sizeof(double) * (size_t)b->nsm * (8 * (size_t)max_iter + 8 + kBatchEllScratch),
                                                         &err));
-    if (err == cudaSuccess) b->counter = static_cast<int *>(balloc(b, 2 * sizeof(int), &err));
+    if (err == cudaSuccess) b->counter = static_cast<int *>(balloc(b, 3 * sizeof(int), &err));
     if (err == cudaSuccess) {
-        b->err = b->counter + 1;
+        b->err = b->counter + 2;
         err = cudaMemcpyAsync(b->d_inst, inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, b->stream);
     }
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(b->counter, 0, 2 * sizeof(int), b->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(b->counter, 0, 3 * sizeof(int), b->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
     if (err != cudaSuccess) {
         release(b);
@@ -202,16 +214,102 @@ osmps_status osmps_ed_batch_set_graph(osmps_ed_batch_t *ob, int enable) {
     return OSMPS_OK;
 }
 
-osmps_status osmps_ed_batch_set_grid(osmps_ed_batch_t *ob, int ctas) {
-    if (ob == nullptr || ctas < 0 || ctas > ob->b.nsm) return OSMPS_EINVAL;
+osmps_status osmps_ed_batch_set_split(osmps_ed_batch_t *ob, int csize, int lsplit) {
+    if (ob == nullptr) return OSMPS_EINVAL;
     BatchHandle *b = &ob->b;
-    const int g = std::min(b->n, ctas == 0 ? b->nsm : ctas);
-    if (g != b->grid && b->graph != nullptr) {
+    if (csize != 1 && csize != 2 && csize != 4 && csize != 8) return OSMPS_EINVAL;
+    int log2c = 0;
+    while ((1 << log2c) < csize) ++log2c;
+    // a cluster CTA's range of a streaming pass must hold a multiple of 1024 vectors
+    const int lmin = 11 + (b->prec == OSMPS_FP64 ? 0 : 1) + log2c;
+    if (csize > 1 && (lsplit < lmin || lsplit > kBatchMaxL)) return OSMPS_EINVAL;
+    int nbig = 0, grid = std::min(b->n, b->nsm);
+    if (csize > 1) {
+        for (int k = 0; k < b->n; ++k)
+            if (b->L[k] >= lsplit) ++nbig;
+        int ncl = 0;
+        cudaError_t err = batch::batch_max_clusters(b->prec, csize, b->nsm, &ncl);
+        if (err != cudaSuccess) return from_cuda(err);
+        if (ncl < 1) return OSMPS_EUNSUPPORTED;
+        grid = csize * std::min(ncl, b->nsm / csize);
+    }
+    if (b->graph != nullptr && (grid != b->grid || csize != b->csize || nbig != b->nbig)) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
-    b->grid = g;
+    b->csize = csize;
+    b->lsplit = csize > 1 ? lsplit : kBatchMaxL + 1;
+    b->nbig = nbig;
+    b->grid = grid;
     return OSMPS_OK;
+}
+
+osmps_status osmps_ed_batch_get_split(const osmps_ed_batch_t *ob, int *csize, int *lsplit, int *grid) {
+    if (ob == nullptr || csize == nullptr || lsplit == nullptr || grid == nullptr) return OSMPS_EINVAL;
+    *csize = ob->b.csize;
+    *lsplit = ob->b.lsplit;
+    *grid = ob->b.grid;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_batch_autotune(osmps_ed_batch_t *ob, void *psi, double tol, double *best_ms) {
+    if (ob == nullptr || psi == nullptr || !(tol >= 0.0) || !std::isfinite(tol)) return OSMPS_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(psi) & 15u) != 0) return OSMPS_EINVAL;
+    BatchHandle *b = &ob->b;
+    const size_t esize = b->prec == OSMPS_FP64 ? 16 : 8;
+    const size_t vbytes = esize * (size_t)b->total;
+    int lmax = 0;
+    for (int k = 0; k < b->n; ++k) lmax = std::max(lmax, b->L[k]);
+    // candidates: no clusters, and clusters of 2, 4, 8 CTAs for the chains with
+    // L >= lmax - 2, lmax - 1 or lmax
+    std::vector<std::pair<int, int>> cand;
+    cand.push_back({1, kBatchMaxL + 1});
+    for (int cs : {2, 4, 8})
+        for (int ls = lmax - 2; ls <= lmax; ++ls) cand.push_back({cs, ls});
+    void *save = nullptr;
+    double *outs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaMalloc(&save, vbytes);
+    if (err == cudaSuccess) err = cudaMalloc(&outs, (size_t)b->n * 4 * sizeof(double));
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(save, psi, vbytes, cudaMemcpyDeviceToDevice, b->stream);
+    const int keep_graph = b->use_graph;
+    b->use_graph = 0;
+    float best = 1e30f;
+    std::pair<int, int> best_c = {b->csize, b->lsplit};
+    osmps_status st = OSMPS_OK;
+    for (size_t i = 0; i < cand.size() && err == cudaSuccess && st == OSMPS_OK; ++i) {
+        if (osmps_ed_batch_set_split(ob, cand[i].first, cand[i].second) != OSMPS_OK) continue;
+        if (cand[i].first > 1 && b->nbig == 0) continue;
+        err = cudaMemcpyAsync(psi, save, vbytes, cudaMemcpyDeviceToDevice, b->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+        if (err == cudaSuccess)
+            err = batch::launch_batch(b, psi, tol, outs, outs + b->n, reinterpret_cast<int *>(outs + 2 * b->n),
+                                      reinterpret_cast<int *>(outs + 3 * b->n));
+        if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) break;
+        st = osmps_ed_batch_check(ob);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_c = cand[i];
+        }
+    }
+    if (err == cudaSuccess) err = cudaMemcpyAsync(psi, save, vbytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
+    b->use_graph = keep_graph;
+    if (e0 != nullptr) cudaEventDestroy(e0);
+    if (e1 != nullptr) cudaEventDestroy(e1);
+    cudaFree(save);
+    cudaFree(outs);
+    if (err != cudaSuccess) return from_cuda(err);
+    if (st != OSMPS_OK) return st;
+    osmps_status s2 = osmps_ed_batch_set_split(ob, best_c.first, best_c.second);
+    if (s2 == OSMPS_OK && best_ms != nullptr) *best_ms = (double)best;
+    return s2;
 }
 
 osmps_status osmps_ed_batch_lanczos_ground(osmps_ed_batch_t *ob, void *psi, double tol, double *energy,

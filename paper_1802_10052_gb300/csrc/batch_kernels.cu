@@ -50,10 +50,13 @@ struct BatchParams {
     V *psi, *R0, *R1, *R2, *X;
     double *energy, *residual;
     int *iters, *status;
-    double *scratch;  // per CTA: 8 * max_iter + 8 + 4096 doubles
-    int *counter, *err;
+    double *scratch;  // per CTA: 8 * max_iter + 8 + kBatchEllScratch doubles
+    int *counter;     // [0] queue of the large chains, [1] queue of the others
+    int *err;
     double tol;
     int n, max_iter;
+    int nbig;         // order[0..nbig) are solved by whole clusters (cluster launches only)
+    int small_first;  // first order index of the one-CTA queue
 };
 
 // ---------------------------------------------------------------------------
@@ -233,6 +236,41 @@ struct RitzState {
     double theta, theta_prev, dtheta, est;
 };
 
+// ---- thread-block cluster primitives (C CTAs sharing one chain) ----
+__device__ __forceinline__ int cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ int cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return (int)r;
+}
+// Every thread of every CTA of the cluster; release/acquire orders the global
+// and shared memory accesses before it with those after it, cluster-wide.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned dsmem_addr(const void *ptr, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(ptr)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double ld_dsmem(const double *ptr, int rank) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(ptr, rank)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_dsmem(int *ptr, int rank, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(dsmem_addr(ptr, rank)), "r"(v) : "memory");
+}
+
+// Launched either without clusters (every CTA solves one chain at a time) or
+// with clusters of C CTAs: the C CTAs of a cluster first solve the large
+// chains order[0..nbig) together (tiles and vector ranges split by rank,
+// reductions exchanged through distributed shared memory, a cluster barrier
+// after each pass), then take the remaining chains one CTA each.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<T> p) {
     typedef typename Cx<T>::v16 V;
@@ -251,37 +289,68 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
     T *Jt = reinterpret_cast<T *>(red + 2 * kWarps);           // J(r) for r <= kMaxL
     __shared__ int s_int[2];
     __shared__ double s_dbl[2];
+    __shared__ double s_slot[2][4];  // cluster reductions, double-buffered
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int csize = cluster_size(), crank = cluster_rank();
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    if (csize > 1) cluster_barrier();  // peers' shared memory exists before any remote access
     unsigned ph = 0u;  // parity of the next wait on each stage (bit s)
+    int par = 0;       // slot set of the next cluster reduction
     const int mi = p.max_iter;
     double *alpha = p.scratch + (size_t)blockIdx.x * (size_t)(8 * mi + 8 + kBatchEllScratch);
-    double *beta = alpha + mi;    // beta[0..mi]
-    double *yv = beta + mi + 1;   // Ritz vector in the Lanczos basis
-    double *work = yv + mi;       // 5 * mi
-    double *ell_scr = work + 5 * mi;  // kBatchEllScratch doubles: E_ll table of the current chain
+    double *beta = alpha + mi;         // beta[0..mi]
+    double *yv = beta + mi + 1;        // Ritz vector in the Lanczos basis
+    double *work = yv + mi;            // 5 * mi
+    double *ell_scr = work + 5 * mi;   // kBatchEllScratch doubles: E_ll table of the current chain
 
-    for (;;) {
-        if (tid == 0) s_int[0] = atomicAdd(p.counter, 1);
-        __syncthreads();
-        const int idx = s_int[0];
-        __syncthreads();
-        if (idx >= p.n) break;
-        const int k = p.order[idx];
+    // Solves chain k with cc CTAs (this one has rank cr); false when a bounded
+    // wait gave up (the decision is the same on every CTA of the group).
+    auto solve = [&](const int k, const int cc, const int cr) -> bool {
         const BatchInst &in = p.inst[k];
         const int L = in.L;
         const int g = L - TBITS, c = TBITS - g;  // pass B: g flipped bits, chunks of 2^c amplitudes
         const int nt = 1 << g;                   // tiles per pass
+        const int ntl = (nt - cr + cc - 1) / cc; // this CTA's tiles per pass: t = cr + l cc
         const long long nvec = (1ll << L) >> LOGVE;
+        const long long vlen = nvec / cc, vbeg = vlen * cr;  // this CTA's range of the streaming passes
         const long long voff = in.off >> LOGVE;
         if (tid <= kMaxL) Jt[tid] = (T)in.J[tid];
         const T hT = (T)in.h;
         __syncthreads();
+
+        // sums over the group: CTA sums, then (cc > 1) the CTAs' slots read in rank order
+        auto gsum = [&](double &a, double &b, double &f) {
+            cta_sum2(a, b, red);
+            if (cc > 1) {
+                if (tid == 0) {
+                    s_slot[par][0] = a;
+                    s_slot[par][1] = b;
+                    s_slot[par][2] = f;
+                }
+                cluster_barrier();
+                double sa = 0.0, sb = 0.0, sf = 0.0;
+                for (int r = 0; r < cc; ++r) {
+                    sa += ld_dsmem(&s_slot[par][0], r);
+                    sb += ld_dsmem(&s_slot[par][1], r);
+                    sf += ld_dsmem(&s_slot[par][2], r);
+                }
+                a = sa;
+                b = sb;
+                f = sf;
+                par ^= 1;
+            }
+        };
+        auto gbar = [&]() {
+            if (cc > 1)
+                cluster_barrier();
+            else
+                __syncthreads();
+        };
 
         // E_ll over the TBITS low bits (same in every tile), a per-CTA table
         // read into registers at the start of every pass A
@@ -322,39 +391,41 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             }
         };
 
-        bool failed = false;
-        // Tile loop over nt tiles: warp 0 keeps kStages copies in flight; body runs on all threads.
+        // Loop over this CTA's tiles l = 0..ntl-1 (tile t = cr + l cc): warp 0
+        // keeps kStages copies in flight; body(t, l, s) runs on all threads.
         auto run_tiles = [&](auto issue, auto body) -> bool {
-            const int pre = nt < kStages ? nt : kStages;
+            const int pre = ntl < kStages ? ntl : kStages;
             if (warp == 0)
-                for (int t = 0; t < pre; ++t) issue(t, t);
-            for (int t = 0; t < nt; ++t) {
-                const int s = t % kStages;
+                for (int l = 0; l < pre; ++l) issue(cr + l * cc, l);
+            for (int l = 0; l < ntl; ++l) {
+                const int s = l % kStages;
                 const bool ok = mbar_wait(&full[s], (ph >> s) & 1u, p.err);
                 ph ^= 1u << s;
                 if (__syncthreads_or(!ok)) {
                     if (tid == 0) {
                         atomicExch(p.err, 1);
                         drain_wait(&full[s], ((ph >> s) & 1u) ^ 1u);
-                        for (int u = t + 1; u < nt && u < t + kStages; ++u)
+                        for (int u = l + 1; u < ntl && u < l + kStages; ++u)
                             drain_wait(&full[u % kStages], (ph >> (u % kStages)) & 1u);
                     }
                     return false;
                 }
-                body(t, s);
+                body(cr + l * cc, l, s);
                 __syncthreads();
-                if (warp == 0 && t + kStages < nt) issue(t + kStages, s);
+                if (warp == 0 && l + kStages < ntl) issue(cr + (l + kStages) * cc, l + kStages);
             }
             return true;
         };
-        auto issue_contig = [&](const V *src, int t, int s) {
+        auto issue_contig = [&](const V *src, int t, int l) {
+            const int s = l % kStages;
             if (lane == 0) {
                 mbar_arrive_expect_tx(&full[s], kTileBytes);
                 bulk_load(U + (size_t)s * kTileVec, src + (size_t)t * kTileVec, kTileBytes, &full[s]);
             }
         };
-        auto issue_gather = [&](const V *src, int m, int s) {
+        auto issue_gather = [&](const V *src, int m, int l) {
             // segment hi: 2^c amplitudes at (hi << TBITS) + (m << c), to tile offset hi << c
+            const int s = l % kStages;
             const unsigned seg = (unsigned)(2 * sizeof(T)) << c;
             if (lane == 0) mbar_arrive_expect_tx(&full[s], kTileBytes);
             __syncwarp();
@@ -377,12 +448,12 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             for (int i = 0; i < kVPT; ++i)
 #pragma unroll
                 for (int e = 0; e < VE; ++e) ell[i * VE + e] = ell_tab[((tid + kThreads * i) << LOGVE) + e];
-            build_tab(0, 0);
+            build_tab(cr, 0);
             __syncthreads();
-            return run_tiles([&](int t, int s) { issue_contig(src, t, s); },
-                             [&](int t, int s) {
+            return run_tiles([&](int t, int l) { issue_contig(src, t, l); },
+                             [&](int t, int l, int s) {
                 const V *Us = U + (size_t)s * kTileVec;
-                const T *ta = tab + (t & 1) * kTabN;
+                const T *ta = tab + (l & 1) * kTabN;
                 const T *tb = ta + kTA;
                 A self[NE];
 #pragma unroll
@@ -452,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
                         }
                     }
                 }
-                if (t + 1 < nt) build_tab(t + 1, (t + 1) & 1);
+                if (l + 1 < ntl) build_tab(t + cc, (l + 1) & 1);
                 acc1 += (mode == MODE_ALPHA ? sc : 1.0) * (double)part1;
                 acc2 += (double)part2;
             });
@@ -469,8 +540,8 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             const T scT = (T)sc;
             const K hk = mkcoef(hT * scT);
             const T thT = (T)theta;
-            return run_tiles([&](int m, int s) { issue_gather(src, m, s); },
-                             [&](int m, int s) {
+            return run_tiles([&](int m, int l) { issue_gather(src, m, l); },
+                             [&](int m, int l, int s) {
                 const V *Us = U + (size_t)s * kTileVec;
                 A wv[NE], f[NE];
 #pragma unroll
@@ -526,11 +597,12 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             });
         };
 
-        // Pass C (streaming): w <- w - a u - b up and |w|^2; x <- x + y u (or y u) and |x|^2.
+        // Pass C (streaming over this CTA's range): w <- w - a u - b up and |w|^2;
+        // x <- x + y u (or y u) and |x|^2.
         auto passC = [&](V *w, const V *u, const V *up, T a, T b, bool use_up, bool do_w, V *x, T y, bool x_init,
                          bool do_x, double &nw, double &nx) {
             const K ka = mkcoef(-a), kb = mkcoef(-b), ky = mkcoef(y);
-            for (long long v0 = tid; v0 < nvec; v0 += 4 * kThreads) {
+            for (long long v0 = vbeg + tid; v0 < vbeg + vlen; v0 += 4 * kThreads) {
                 V uv[4], wv[4], pv[4], xv[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -583,11 +655,20 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             asm volatile("fence.proxy.async.global;" ::: "memory");
         };
 
-        // one H.psi product (passes A and B) into w
+        // one H.psi product (passes A and B) into w; false, the same on every
+        // CTA of the group, when a bounded wait gave up
         auto hpsi = [&](const V *u, V *w, double sc, bool want_alpha, double &al) -> bool {
             double a1 = 0.0, a2 = 0.0;
             bool ok = passA(u, w, sc, (want_alpha && g == 0) ? MODE_ALPHA : MODE_STORE, 0.0, a1, a2);
-            if (ok && g > 0) ok = passB(u, w, sc, want_alpha ? MODE_ALPHA : MODE_STORE, 0.0, a1, a2);
+            if (g > 0) {
+                if (cc > 1) {  // pass B reads partial sums written by every CTA of the group
+                    double z1 = 0.0, z2 = 0.0, f = ok ? 0.0 : 1.0;
+                    gsum(z1, z2, f);
+                    ok = f == 0.0;
+                }
+                if (!ok) return false;
+                ok = passB(u, w, sc, want_alpha ? MODE_ALPHA : MODE_STORE, 0.0, a1, a2);
+            }
             al = a1;
             return ok;
         };
@@ -599,13 +680,14 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
         // tridiagonal work is then comparable to a step)
         const int chk = L >= 17 ? 1 : (L == 16 ? 2 : (L == 15 ? 4 : 8));
         int status = 0;
+        const bool lead = (cr == 0 && tid == 0);
 
         // |psi|^2 of the start vector
-        double n0 = 0.0;
-        for (long long v0 = tid; v0 < nvec; v0 += 16 * kThreads) {  // nvec is a multiple of 4096
+        double n0 = 0.0, zz = 0.0, f0 = 0.0;
+        for (long long v0 = vbeg + tid; v0 < vbeg + vlen; v0 += 4 * kThreads) {
             T part = (T)0;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 A a[VE];
                 unpackv(u0[v0 + q * kThreads], a);
 #pragma unroll
@@ -613,15 +695,15 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             }
             n0 += (double)part;
         }
-        n0 = cta_sum(n0, red);
+        gsum(n0, zz, f0);
         if (!(n0 > 0.0) || !isfinite(n0)) {
-            if (tid == 0) {
+            if (lead) {
                 p.status[k] = OSMPS_EINVAL;
                 p.energy[k] = 0.0;
                 p.residual[k] = 0.0;
                 p.iters[k] = 0;
             }
-            continue;
+            return true;
         }
         const double s0 = 1.0 / sqrt(n0);
 
@@ -641,15 +723,13 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             const V *uc = j == 0 ? u0 : Rb[(j - 1) % 3];
             const V *upv = j <= 1 ? u0 : Rb[(j - 2) % 3];
             V *w = Rb[j % 3];
-            double al = 0.0;
-            if (!hpsi(uc, w, sc, true, al)) {
-                failed = true;
-                break;
-            }
-            al = cta_sum(al, red);
-            double nw = 0.0, nx = 0.0;
+            double al = 0.0, z = 0.0;
+            double f = hpsi(uc, w, sc, true, al) ? 0.0 : 1.0;
+            gsum(al, z, f);
+            if (f != 0.0) return false;
+            double nw = 0.0, nx = 0.0, z2 = 0.0;
             passC(w, uc, upv, (T)(al * sc), (T)(bcur * sp), j > 0, true, nullptr, (T)0, false, false, nw, nx);
-            nw = cta_sum(nw, red);
+            gsum(nw, nx, z2);
             const double bn = sqrt(nw);
             if (tid == 0) {
                 alpha[j] = al;
@@ -693,10 +773,6 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             sc = 1.0 / bn;
             bcur = bn;
         }
-        if (failed) {
-            if (tid == 0) p.status[k] = OSMPS_ETIMEOUT;
-            break;
-        }
         if (!conv) status = OSMPS_ENOCONV;
         if (m_best != m) {  // Ritz vector of T_{m_best}
             if (tid == 0) ritz_vector(alpha, beta, m_best, theta_best, yv, work);
@@ -716,32 +792,28 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             const T yT = (T)(yv[j] * sc);
             double nw = 0.0, nx = 0.0;
             if (j == mv - 1) {
+                double z = 0.0, zf = 0.0;
                 passC(w, uc, upv, (T)0, (T)0, false, false, Xb, yT, j == 0, true, nw, nx);
-                nxs = cta_sum(nx, red);
+                gsum(nx, z, zf);
+                nxs = nx;
                 break;
             }
-            double al = 0.0;
-            if (!hpsi(uc, w, sc, false, al)) {
-                failed = true;
-                break;
-            }
+            double al = 0.0, z1 = 0.0, z2 = 0.0;
+            double f = hpsi(uc, w, sc, false, al) ? 0.0 : 1.0;
+            if (cc > 1) gsum(z1, z2, f);  // pass C reads w of every CTA's tiles
+            if (f != 0.0) return false;
             passC(w, uc, upv, (T)(alpha[j] * sc), (T)(bcur * sp), j > 0, true, Xb, yT, j == 0, true, nw, nx);
-            __syncthreads();
+            gbar();  // the next pass A reads u written by every CTA of the group
             const double bn = beta[j + 1];
             sp = sc;
             sc = 1.0 / bn;
             bcur = bn;
         }
-        if (failed) {
-            if (tid == 0) p.status[k] = OSMPS_ETIMEOUT;
-            break;
-        }
 
         // psi <- x / |x|
-        const T xs = (T)(1.0 / sqrt(nxs));
         {
-            const K kx = mkcoef(xs);
-            for (long long v = tid; v < nvec; v += kThreads) {
+            const K kx = mkcoef((T)(1.0 / sqrt(nxs)));
+            for (long long v = vbeg + tid; v < vbeg + vlen; v += kThreads) {
                 A a[VE];
                 unpackv(Xb[v], a);
 #pragma unroll
@@ -750,25 +822,67 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
             }
             asm volatile("fence.proxy.async.global;" ::: "memory");
         }
-        __syncthreads();
+        gbar();
 
         // true residual |H psi - theta psi| and <psi, H psi>
         double r2 = 0.0, rq = 0.0;
         bool ok = passA(u0, Rb[0], 1.0, g == 0 ? MODE_RESID : MODE_STORE, rs.theta, r2, rq);
-        if (ok && g > 0) ok = passB(u0, Rb[0], 1.0, MODE_RESID, rs.theta, r2, rq);
-        if (!ok) {
-            if (tid == 0) p.status[k] = OSMPS_ETIMEOUT;
-            break;
+        if (g > 0) {
+            if (cc > 1) {
+                double z1 = 0.0, z2 = 0.0, f = ok ? 0.0 : 1.0;
+                gsum(z1, z2, f);
+                ok = f == 0.0;
+            }
+            if (!ok) return false;
+            ok = passB(u0, Rb[0], 1.0, MODE_RESID, rs.theta, r2, rq);
         }
-        cta_sum2(r2, rq, red);
-        if (tid == 0) {
+        double fr = ok ? 0.0 : 1.0;
+        gsum(r2, rq, fr);
+        if (fr != 0.0) return false;
+        if (lead) {
             p.energy[k] = rs.theta;
             p.residual[k] = sqrt(fmax(r2, 0.0));
             p.iters[k] = m;
             p.status[k] = status;
         }
         __syncthreads();
+        return true;
+    };
+
+    // ---- work queues: large chains per cluster, then one chain per CTA ----
+    bool big = csize > 1 && p.nbig > 0;
+    for (;;) {
+        int idx, cc, cr;
+        if (big) {
+            if (crank == 0 && tid == 0) {
+                const int v = atomicAdd(&p.counter[0], 1);
+                for (int r = 0; r < csize; ++r) st_dsmem(&s_int[0], r, v);
+            }
+            cluster_barrier();
+            idx = s_int[0];
+            cluster_barrier();
+            if (idx >= p.nbig) {
+                big = false;
+                continue;
+            }
+            cc = csize;
+            cr = crank;
+        } else {
+            if (tid == 0) s_int[1] = atomicAdd(&p.counter[1], 1);
+            __syncthreads();
+            idx = p.small_first + s_int[1];
+            __syncthreads();
+            if (idx >= p.n) break;
+            cc = 1;
+            cr = 0;
+        }
+        const int k = p.order[idx];
+        if (!solve(k, cc, cr)) {
+            if (cr == 0 && tid == 0) p.status[k] = OSMPS_ETIMEOUT;
+            break;
+        }
     }
+    if (csize > 1) cluster_barrier();  // no CTA leaves while a peer may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -801,10 +915,29 @@ static cudaError_t launch_batch_t(BatchHandle *b, void *psi, double tol, double 
     p.tol = tol;
     p.n = b->n;
     p.max_iter = b->max_iter;
+    p.nbig = b->csize > 1 ? b->nbig : 0;
+    p.small_first = p.nbig;
     const size_t smem = batch_smem_bytes(b->prec);
-    cudaError_t err = cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream);
+    cudaError_t err = cudaMemsetAsync(b->counter, 0, 2 * sizeof(int), b->stream);
     if (err != cudaSuccess) return err;
-    lanczos_batch_kernel<T><<<b->grid, kThreads, smem, b->stream>>>(p);
+    if (b->csize > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)b->grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = b->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)b->csize;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        err = cudaLaunchKernelEx(&cfg, lanczos_batch_kernel<T>, p);
+        if (err != cudaSuccess) return err;
+    } else {
+        lanczos_batch_kernel<T><<<b->grid, kThreads, smem, b->stream>>>(p);
+    }
     b->launches++;
     return cudaGetLastError();
 }
@@ -816,6 +949,24 @@ cudaError_t batch_prepare(int prec) {
     return prec == OSMPS_FP64
                ? cudaFuncSetAttribute(lanczos_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
                : cudaFuncSetAttribute(lanczos_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// Clusters of csize CTAs that can be resident at once (one CTA per SM).
+cudaError_t batch_max_clusters(int prec, int csize, int nsm, int *out) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(csize * (nsm / csize)));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = batch_smem_bytes(prec);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return prec == OSMPS_FP64
+               ? cudaOccupancyMaxActiveClusters(out, (void *)lanczos_batch_kernel<double>, &cfg)
+               : cudaOccupancyMaxActiveClusters(out, (void *)lanczos_batch_kernel<float>, &cfg);
 }
 
 cudaError_t launch_batch(BatchHandle *b, void *psi, double tol, double *energy, double *residual, int *iters,

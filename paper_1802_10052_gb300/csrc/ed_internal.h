@@ -193,15 +193,19 @@ struct BatchHandle {
     int prec;
     int max_iter;
     int grid;                           // CTAs of the persistent launch
+    int csize;                          // CTAs per cluster (1: no clusters)
+    int lsplit;                         // chains with L >= lsplit are solved by whole clusters
+    int nbig;                           // number of such chains (first in the work order)
     cudaStream_t stream;
     long long total;                    // packed state length (amplitudes)
     long long *offsets;                 // host, n + 1
+    int *L;                             // host, chain lengths
     BatchInst *d_inst;
     int *d_order;                       // chain order of the work queue (largest first)
     void *R[3];                         // recurrence vectors (packed like the states)
     void *X;                            // Ritz vector accumulator
     double *scratch;                    // per CTA: alpha, beta, y, tridiagonal work
-    int *counter;                       // work-queue head
+    int *counter;                       // work-queue heads: [0] large chains, [1] the others
     int *err;                           // raised when a bounded wait gives up
     uint64_t owned_bytes;
     uint64_t launches;
@@ -218,6 +222,7 @@ namespace batch {
 size_t batch_smem_bytes(int prec);
 int batch_tile_bits(int prec);
 cudaError_t batch_prepare(int prec);
+cudaError_t batch_max_clusters(int prec, int csize, int nsm, int *out);
 cudaError_t launch_batch(BatchHandle *b, void *psi, double tol, double *energy, double *residual, int *iters,
                          int *status);
 }  // namespace batch

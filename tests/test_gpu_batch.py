@@ -97,6 +97,32 @@ def test_batch_rerun_and_graph_replay_are_bit_identical():
     b.close()
 
 
+@pytest.mark.parametrize("csize,lsplit", [(2, 15), (4, 16), (8, 17)])
+def test_batch_cluster_split_matches_oracle(csize, lsplit):
+    """Long chains solved by whole thread-block clusters (tiles and vector
+    ranges split over the CTAs, reductions through distributed shared memory),
+    the rest one per CTA: every chain against the oracle, and a rerun is
+    bit-identical."""
+    rng = np.random.Generator(np.random.Philox(23))
+    Ls = [18, 17, 16, 15, 14, 18, 16, 14]
+    alphas = [float(a) for a in rng.uniform(0.5, 3.0, size=len(Ls))]
+    hs = [float(x) for x in rng.uniform(0.2, 2.0, size=len(Ls))]
+    b = ChainBatch(Ls, [1.0] * len(Ls), alphas, hs, prec="mixed", max_iter=800)
+    b.set_split(csize, lsplit)
+    cs, ls, grid = b.get_split()
+    assert cs == csize and ls == lsplit and grid % csize == 0 and grid >= csize
+    start = pack(si.batch_start_states(Ls, seed=13), "mixed")
+    psi = start.clone()
+    E, R, it, st = b.lanczos_ground(psi, tol=1e-10)
+    assert (st == 0).all(), st
+    for k in range(len(Ls)):
+        check_chain(b, psi, k, Ls[k], alphas[k], hs[k], E, R, "mixed")
+    psi2 = start.clone()
+    E2, R2, it2, st2 = b.lanczos_ground(psi2, tol=1e-10)
+    assert np.array_equal(E, E2) and torch.equal(psi, psi2)
+    b.close()
+
+
 def test_batch_full_size_512_chains():
     """512 long-range chains, L ~ U{14..20}, alpha ~ U[0.5, 3], h ~ U[0.2, 2],
     each Lanczos to 1e-10 in one persistent launch (complex64 vectors, FP64
@@ -108,6 +134,10 @@ def test_batch_full_size_512_chains():
     hs = [x[2] for x in inst]
     b = ChainBatch(Ls, [1.0] * 512, alphas, hs, prec="mixed", max_iter=1000)
     psi = pack(si.batch_start_states(Ls, seed=3), "mixed")
+    start = psi.clone()
+    cs, ls, grid, best = b.autotune(psi, tol=1e-10)
+    print(f"autotune: clusters of {cs} for L >= {ls}, grid {grid}, {best:.1f} ms")
+    assert torch.equal(psi, start)  # the tuner restores the start vectors
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     E, R, it, st = b.lanczos_ground(psi, tol=1e-10)
