@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hpsi28", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -270,6 +271,91 @@ def hpsi_L28(prec, reps=20, warm=3):
             "frac_of_measured_hbm": alg / (t * 1e-3) / 1e9 / peak, "algorithmic_bytes": alg}
 
 
+def batched_ground(n=512, reps=3):
+    """Batched ground states: n long-range chains, L ~ U{14..20}, alpha ~ U[0.5, 3],
+    h ~ U[0.2, 2] (seed 3), each Lanczos to 1e-10, in one persistent launch
+    replayed from a CUDA graph (work split chosen by the autotuner).  Beside it:
+    the same batch in FP64, and the plain single-chain solver (FP64, and
+    complex64 to a 1e-4 explicit residual) timed on a stratified sample of two
+    chains per length and scaled by the length counts."""
+    import numpy as np
+    import torch
+
+    import seeded_inputs as si
+    from paper_1802_10052_gb300 import Chain, ChainBatch
+
+    inst = si.batched_instances(n, seed=3)
+    Ls = [x[0] for x in inst]
+    al = [x[1] for x in inst]
+    hs = [x[2] for x in inst]
+    starts = si.batch_start_states(Ls, seed=3)
+    out = {"workload": f"{n} chains H = sum |i-j|^-alpha sz sz + h sum sx, L~U{{14..20}}, alpha~U[0.5,3], "
+                       "h~U[0.2,2], seeded Gaussian starts, Lanczos tol 1e-10"}
+
+    def timed_batch(prec, reps_):
+        dt = np.complex64 if prec == "mixed" else np.complex128
+        b = ChainBatch(Ls, [1.0] * n, al, hs, prec=prec, max_iter=1000)
+        start = torch.from_numpy(np.concatenate([v.astype(dt) for v in starts])).cuda()
+        psi = start.clone()
+        split = b.autotune(psi, tol=1e-10) if prec == "mixed" else b.get_split() + (None,)
+        b.set_graph(True)
+        ts = []
+        for r in range(reps_ + 1):
+            psi.copy_(start)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.lanczos_ground_async(psi, 1e-10)
+            e1.record()
+            b.check()
+            if r > 0:
+                ts.append(e0.elapsed_time(e1))
+        it = b.iters.cpu().numpy().astype(np.float64)
+        st = b.status.cpu().numpy()
+        E = b.energy.cpu().numpy()
+        R = b.residual.cpu().numpy()
+        D = np.array([1 << L for L in Ls], dtype=np.float64)
+        esize = 8 if prec == "mixed" else 16
+        t = float(np.median(ts))
+        res = {"ms": t, "chains_per_s": n / (t * 1e-3), "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+               "converged": int((st == 0).sum()), "max_residual": float(R.max()),
+               "algorithmic_GBps": float(np.sum(esize * D * (20 * it + 7))) / (t * 1e-3) / 1e9,
+               "split": {"cluster_ctas": split[0], "cluster_min_L": split[1], "grid": split[2]},
+               "launches_per_solve": 1}
+        b.close()
+        return res, E
+
+    mixed, E_mixed = timed_batch("mixed", reps)
+    fp64, E_fp64 = timed_batch("fp64", 1)
+    out["batched_mixed"] = mixed
+    out["batched_fp64"] = fp64
+    out["max_rel_energy_diff_mixed_vs_fp64"] = float(np.max(np.abs(E_mixed - E_fp64) / np.maximum(1.0, np.abs(E_fp64))))
+    counts = {L: Ls.count(L) for L in sorted(set(Ls))}
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-4)):
+        per = {}
+        for L in counts:
+            ts = []
+            for k in [k for k in range(n) if Ls[k] == L][:2]:
+                c = Chain(L, J=1.0, alpha=al[k], h=hs[k], prec=prec)
+                x = torch.from_numpy(starts[k].astype(np.complex128 if prec == "fp64" else np.complex64)).cuda()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c.lanczos_ground(x, tol=tol, max_iter=1000, raise_on_noconv=False)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                c.close()
+            per[L] = float(np.mean(ts))
+        est = sum(per[L] * counts[L] for L in counts)
+        out[f"plain_{prec}"] = {"s_scaled_to_batch": est, "tol_explicit_residual": tol,
+                                "sample": "2 chains per length, mean time x chains of that length",
+                                "s_per_chain_by_L": per}
+    out["speedup_batched_mixed_vs_plain_fp64"] = out["plain_fp64"]["s_scaled_to_batch"] / (mixed["ms"] * 1e-3)
+    out["speedup_batched_fp64_vs_plain_fp64"] = out["plain_fp64"]["s_scaled_to_batch"] / (fp64["ms"] * 1e-3)
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -384,6 +470,8 @@ def main():
     extra = {}
     if rank == 0 and not args.no_hpsi28:
         extra["hpsi_L28"] = [hpsi_L28("mixed"), hpsi_L28("fp64", reps=6)]
+    if rank == 0 and not args.no_batch:
+        extra["batched_ground_512"] = batched_ground()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_line()
