@@ -173,6 +173,36 @@ osmps_status osmps_ed_krylov_evolve(osmps_ed_t *ed, void *psi, double dt, int ns
                                     double tol, double *err_estimate);
 
 /*
+ * Gradient of a final energy under a piecewise-constant field (the paper has
+ * no gradients; this is the adjoint of its Krylov time evolution, Sec. III.D).
+ * With H(h) = H_zz + h X (H_zz the handle's couplings, X = sum_k sigma^x_k),
+ *     psi_k = exp(-i dt H(h_k)) psi_{k-1},  k = 1..nsteps,  psi_0 = psi0,
+ *     loss  = <psi_N| H(h_target) |psi_N>,
+ * returns loss and, unless both pointers are NULL, d loss / d h_k for every
+ * step and d loss / d s, s the overall scale of the couplings (J(r) -> s J(r)
+ * at s = 1, in H(h_k) and in the target; for J(r) = J / r^alpha this is
+ * J d loss / d J).  The forward steps are Krylov steps of dimension m as in
+ * osmps_ed_krylov_evolve.  Backward sweep: lambda_N = H(h_target) psi_N,
+ * lambda_{k-1} = exp(+i dt H(h_k)) lambda_k, and
+ *     d loss / d h_k = 2 Re <lambda_k| L(A_k, -i dt X) psi_{k-1}>,
+ * with L(A, E) = int_0^1 e^{sA} E e^{(1-s)A} ds the Frechet derivative of the
+ * exponential at A_k = -i dt H(h_k), evaluated by nquad-point Gauss-Legendre
+ * quadrature in s on Krylov representations of psi_{k-1} and lambda_k
+ * (likewise with E = -i dt H_zz for the coupling scale).  Forward states are
+ * checkpointed every `stride` steps and recomputed segment by segment.
+ *   psi0        device state (not modified).
+ *   h_steps     host array of nsteps fields.
+ *   grad_h      host array of nsteps (may be NULL); grad_scale host (may be NULL).
+ *   nquad       1..32 (8 resolves dt |H| up to ~3 to 1e-14).
+ * Allocates (1 + nsteps/stride + stride + 5) state vectors and a second
+ * Krylov workspace for the call, frees them before returning, and leaves the
+ * handle's fields as they were.  Synchronises.
+ */
+osmps_status osmps_ed_adjoint_grad(osmps_ed_t *ed, const void *psi0, int nsteps, double dt,
+                                   const double *h_steps, int m, double h_target, int stride,
+                                   int nquad, double *loss, double *grad_h, double *grad_scale);
+
+/*
  * <sz_k> for k = 1..L (Sec. IV, Tr(sz rho_k) from the single-site reduced
  * density matrix).  sz: host array of L doubles.  Unnormalised: for a state of
  * norm n the values scale with n^2.  Synchronises.

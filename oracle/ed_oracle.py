@@ -344,6 +344,65 @@ def evolve(make_matvec, psi0: np.ndarray, dt: float, nsteps: int, m: int, field_
     return psi
 
 
+# ---------------------------------------------------------------------------
+# Gradient of a final energy under a piecewise-constant field (the paper has
+# no gradients: the derivative of its Krylov/expm time evolution, Sec. III.D)
+# ---------------------------------------------------------------------------
+
+def final_energy_gradient_dense(L: int, Jr: np.ndarray, h_steps, dt: float, h_target: float, psi0: np.ndarray):
+    """Exact loss = <psi_N|H(h_target)|psi_N> with psi_k = expm(-i dt H(h_k)) psi_{k-1},
+    H(h) = H_zz + h X, and its gradients with respect to every h_k and to the overall
+    coupling scale s (J(r) -> s J(r) at s = 1, in the dynamics and in the target).
+
+    dloss/dtheta = 2 Re sum_k <lambda_k| dU_k/dtheta |psi_{k-1}> (+ the target's own
+    <psi_N|H_zz|psi_N> for s), lambda_N = H(h_target) psi_N, lambda_{k-1} = U_k^H lambda_k.
+    dU_k/dtheta is the Frechet derivative of expm at A_k = -i dt H(h_k) in the
+    direction E = dA_k/dtheta, read off the block-triangular exponential
+    expm([[A, E], [0, A]]) = [[expm(A), L(A, E)], [0, expm(A)]] (Van Loan 1978).
+    Dense: small L only.  Returns (loss, grad_h, grad_scale)."""
+    Hzz = hamiltonian_dense(L, Jr, 0.0)
+    X = hamiltonian_dense(L, np.zeros_like(Jr), 1.0)
+    D = 1 << L
+    hs = [float(x) for x in h_steps]
+    U = [sla.expm(-1j * dt * (Hzz + hk * X)) for hk in hs]
+    psis = [np.asarray(psi0, dtype=np.complex128)]
+    for Uk in U:
+        psis.append(Uk @ psis[-1])
+    HT = Hzz + h_target * X
+    psiN = psis[-1]
+    loss = float(np.real(np.vdot(psiN, HT @ psiN)))
+    lam = HT @ psiN
+    grad_h = np.zeros(len(hs))
+    gscale = float(np.real(np.vdot(psiN, Hzz @ psiN)))
+    Z = np.zeros((D, D), dtype=np.complex128)
+    for k in range(len(hs), 0, -1):
+        A = -1j * dt * (Hzz + hs[k - 1] * X)
+        for E, which in ((-1j * dt * X, "h"), (-1j * dt * Hzz, "s")):
+            big = sla.expm(np.block([[A, E], [Z, A]]))
+            Lk = big[:D, D:]
+            val = 2.0 * float(np.real(np.vdot(lam, Lk @ psis[k - 1])))
+            if which == "h":
+                grad_h[k - 1] = val
+            else:
+                gscale += val
+        lam = U[k - 1].conj().T @ lam
+    return loss, grad_h, gscale
+
+
+def final_energy_krylov(L: int, Jr: np.ndarray, h_steps, dt: float, m: int, h_target: float, psi0: np.ndarray,
+                        scale: float = 1.0) -> float:
+    """The same loss with every step taken by ``krylov_step`` (CSR products), couplings
+    scaled by ``scale``: the forward model whose central differences give reference
+    gradients beyond dense sizes."""
+    Hzz = hamiltonian_csr(L, scale * np.asarray(Jr, dtype=np.float64), 0.0)
+    X = hamiltonian_csr(L, np.zeros_like(np.asarray(Jr, dtype=np.float64)), 1.0)
+    psi = np.asarray(psi0, dtype=np.complex128)
+    for hk in h_steps:
+        hk = float(hk)
+        psi, _ = krylov_step(lambda v: Hzz @ v + hk * (X @ v), psi, dt, m)
+    return float(np.real(np.vdot(psi, Hzz @ psi + h_target * (X @ psi))))
+
+
 def exact_propagate_dense(H: np.ndarray, psi: np.ndarray, t: float) -> np.ndarray:
     """exp(-i H t) psi by the dense matrix exponential (method 1, Sec. III.A)."""
     return sla.expm(-1j * t * H) @ psi

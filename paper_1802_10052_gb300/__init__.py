@@ -20,7 +20,7 @@ import numpy as np
 
 from ._binding import (LIB_PATH, OSMPS_ENOCONV, OSMPS_FP64, OSMPS_MIXED, OSMPS_OK, OsmpsError, check, lib)
 
-__all__ = ["Chain", "ChainBatch", "OsmpsError", "LIB_PATH", "lib"]
+__all__ = ["Chain", "ChainBatch", "FinalEnergy", "OsmpsError", "LIB_PATH", "lib"]
 
 _PREC = {"fp64": OSMPS_FP64, "mixed": OSMPS_MIXED}
 
@@ -170,6 +170,24 @@ class Chain:
                                          C.byref(err)), "osmps_ed_krylov_evolve")
         return err.value
 
+    def adjoint_grad(self, psi0, h_steps, dt, m=20, h_target=1.0, stride=None, nquad=8, want_grad=True):
+        """Loss <psi_N|H(h_target)|psi_N> after the steps exp(-i dt H(h_k)) from psi0, and
+        (if want_grad) d loss/d h_k and d loss/d s (s = overall coupling scale).
+        Returns (loss, grad_h ndarray, grad_scale) or (loss, None, None)."""
+        self._check_state(psi0)
+        hs = np.ascontiguousarray(np.asarray(h_steps, dtype=np.float64))
+        n = hs.size
+        stride = int(stride) if stride is not None else max(1, int(round(math.sqrt(n))))
+        loss = C.c_double()
+        gh = np.zeros(n, dtype=np.float64) if want_grad else None
+        gs = C.c_double()
+        hp = hs.ctypes.data_as(C.POINTER(C.c_double))
+        gp = gh.ctypes.data_as(C.POINTER(C.c_double)) if want_grad else None
+        check(lib.osmps_ed_adjoint_grad(self._h, _dptr(psi0), n, float(dt), hp, int(m), float(h_target), stride,
+                                        int(nquad), C.byref(loss), gp, C.byref(gs) if want_grad else None),
+              "osmps_ed_adjoint_grad")
+        return (loss.value, gh, gs.value) if want_grad else (loss.value, None, None)
+
     def measure_local(self, psi):
         self._check_state(psi)
         out = np.zeros(self.L)
@@ -313,3 +331,46 @@ class ChainBatch:
         self.check()
         return (self.energy.cpu().numpy(), self.residual.cpu().numpy(), self.iters.cpu().numpy(),
                 self.status.cpu().numpy())
+
+
+def _make_final_energy():
+    torch = _torch()
+
+    class FinalEnergy(torch.autograd.Function):
+        """loss = <psi_N|H(h_target)|psi_N> as a differentiable function of the per-step
+        fields h (1-D float64 tensor) and the coupling scale s (0-D float64 tensor, the
+        factor on the chain's couplings; pass ones to differentiate at the chain as built).
+        The backward pass runs the adjoint sweep of the library (osmps_ed_adjoint_grad).
+        Only s = 1 is supported (the chain's couplings are fixed at create)."""
+
+        @staticmethod
+        def forward(ctx, h, s, chain, psi0, dt, m, h_target):
+            if float(s) != 1.0:
+                raise ValueError("FinalEnergy differentiates at coupling scale 1 (build the chain with the couplings)")
+            loss, _, _ = chain.adjoint_grad(psi0, h.detach().cpu().numpy(), dt, m, h_target, want_grad=False)
+            ctx.chain, ctx.psi0, ctx.dt, ctx.m, ctx.h_target = chain, psi0, dt, m, h_target
+            ctx.save_for_backward(h)
+            return torch.tensor(loss, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            (h,) = ctx.saved_tensors
+            _, gh, gs = ctx.chain.adjoint_grad(ctx.psi0, h.detach().cpu().numpy(), ctx.dt, ctx.m, ctx.h_target)
+            gf = float(g)
+            return (torch.from_numpy(gh * gf).to(h.dtype), torch.tensor(gs * gf, dtype=torch.float64),
+                    None, None, None, None, None)
+
+    return FinalEnergy
+
+
+class _Lazy:
+    def __init__(self):
+        self._cls = None
+
+    def apply(self, *a):
+        if self._cls is None:
+            self._cls = _make_final_energy()
+        return self._cls.apply(*a)
+
+
+FinalEnergy = _Lazy()

@@ -9,6 +9,8 @@
 #include <cstddef>
 #include <cstring>
 #include <new>
+#include <vector>
+#include <algorithm>
 
 #include "ed_internal.h"
 
@@ -204,6 +206,57 @@ osmps_status lanczos_iteration(Handle *h, int j, int reorth) {
     }
     CK(launch_ctl_after_update(h, h->ctl, h->partials, np, j, 0));
     return OSMPS_OK;
+}
+
+// Krylov basis of v0 under the handle's current H (m three-term Lanczos steps;
+// the basis and T stay in the handle until the next basis is built).
+osmps_status krylov_basis(Handle *h, void *v0, int m) {
+    CKS(ensure_basis(h, m));
+    CKS(upload_basis_table(h, v0, m));
+    ctl_init_kernel<<<1, 1, 0, h->stream>>>(h->ctl, 1e-12);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    int np = 0;
+    CK(launch_norm2(h, v0, h->partials, &np));
+    CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, m));
+    for (int j = 0; j < m; ++j) CKS(lanczos_iteration(h, j, h->reorth));
+    return OSMPS_OK;
+}
+
+// out = |v0| V exp(-i tau T) e_1 from the current basis (any real tau; the
+// basis is left untouched, so several tau can follow one basis).
+osmps_status krylov_combine(Handle *h, int m, double tau, void *out) {
+    int np = 0;
+    CK(launch_tridiag_exp(h, h->ctl, m, tau));
+    CK(launch_combine(h, h->V_dev, m, out, h->ctl, h->partials, &np));
+    return OSMPS_OK;
+}
+
+// Gauss-Legendre nodes x and weights w on [0, 1]: Newton's method on the
+// Legendre polynomial P_q (three-term recurrence), mapped from [-1, 1].
+void gauss_legendre01(int q, double *x, double *w) {
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(3.14159265358979323846 * (i + 0.75) / (q + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;  // P_0, P_1
+            for (int j = 2; j <= q; ++j) {
+                const double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (q == 1) {
+                p1 = z;
+                p0 = 1.0;
+            }
+            dp = q * (z * p1 - p0) / (z * z - 1.0);  // P_q'(z)
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1.0 + z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // 2 / ((1 - z^2) P'^2), times 1/2 for [0, 1]
+    }
 }
 
 osmps_status check_state_ptr(const Handle *h, const void *p) {
@@ -693,6 +746,189 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
     CK(cudaMemcpyAsync(&Sv, h->lam_dev + nn, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (S) *S = Sv;
+    return OSMPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint gradient of a final energy (see include/osmps_ed.h)
+// ---------------------------------------------------------------------------
+osmps_status osmps_ed_adjoint_grad(osmps_ed_t *ed, const void *psi0, int nsteps, double dt, const double *h_steps,
+                                   int m, double h_target, int stride, int nquad, double *loss, double *grad_h,
+                                   double *grad_scale) {
+    if (ed == nullptr || h_steps == nullptr || loss == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi0));
+    if (nsteps < 1 || !std::isfinite(dt) || m < 1 || m > kMaxKrylov || !std::isfinite(h_target) || stride < 1 ||
+        nquad < 1 || nquad > 32)
+        return OSMPS_EINVAL;
+    for (int k = 0; k < nsteps; ++k)
+        if (!std::isfinite(h_steps[k])) return OSMPS_EINVAL;
+    const bool want_grad = grad_h != nullptr || grad_scale != nullptr;
+    double hb_save[kMaxL + 1];
+    std::memcpy(hb_save, h->hbit, sizeof(hb_save));
+    const size_t vb = vec_bytes(h);
+    const int ncp = (nsteps + stride - 1) / stride + 1;  // checkpoints psi_0, psi_stride, ...
+    // device buffers of this call: checkpoints, one segment of states, lambda, two node states, two products, dots
+    std::vector<void *> bufs;
+    osmps_status st = OSMPS_OK;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (st == OSMPS_OK && cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st = OSMPS_ENOMEM;
+            return nullptr;
+        }
+        bufs.push_back(p);
+        return p;
+    };
+    std::vector<void *> cp(ncp), seg(stride);
+    for (int i = 0; i < ncp; ++i) cp[i] = alloc(vb);
+    void *x = alloc(vb);
+    void *lam = nullptr, *ps = nullptr, *ls = nullptr, *w1 = nullptr, *w0 = nullptr;
+    double *zd = nullptr;
+    if (want_grad) {
+        for (int i = 0; i < stride; ++i) seg[i] = alloc(vb);
+        lam = alloc(vb);
+        ps = alloc(vb);
+        ls = alloc(vb);
+        w1 = alloc(vb);
+        w0 = alloc(vb);
+        zd = static_cast<double *>(alloc(sizeof(double) * 4 * 32));
+    }
+    osmps_ed_t *sib = nullptr;  // second handle: Krylov basis of the adjoint state
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->stream);
+        for (void *p : bufs)
+            if (p != nullptr) cudaFree(p);
+        if (sib != nullptr) osmps_ed_destroy(sib);
+        std::memcpy(h->hbit, hb_save, sizeof(hb_save));
+    };
+    auto fail = [&](osmps_status e) {
+        cleanup();
+        return e;
+    };
+    if (st != OSMPS_OK) return fail(st);
+#define CKA(expr)                              \
+    do {                                       \
+        osmps_status _s = (expr);              \
+        if (_s != OSMPS_OK) return fail(_s);   \
+    } while (0)
+#define CKAC(expr)                                   \
+    do {                                             \
+        cudaError_t _e = (expr);                     \
+        if (_e != cudaSuccess) return fail(from_cuda(_e)); \
+    } while (0)
+    auto set_h = [&](Handle *hh, double v) {
+        for (int b = 0; b < hh->L; ++b) hh->hbit[b] = v;
+    };
+    // one Krylov step of the forward propagation: v <- exp(-i dt H(h_k)) v
+    auto step = [&](void *v, double hk) -> osmps_status {
+        set_h(h, hk);
+        return osmps_ed_krylov_evolve(ed, v, dt, 1, m, 0.0, nullptr);
+    };
+
+    // ---- forward sweep with checkpoints ----
+    CKAC(cudaMemcpyAsync(x, psi0, vb, cudaMemcpyDeviceToDevice, h->stream));
+    CKAC(cudaMemcpyAsync(cp[0], psi0, vb, cudaMemcpyDeviceToDevice, h->stream));
+    for (int k = 1; k <= nsteps; ++k) {
+        CKA(step(x, h_steps[k - 1]));
+        if (k % stride == 0) CKAC(cudaMemcpyAsync(cp[k / stride], x, vb, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    // loss and the direct coupling-scale term: <psi_N| H_target |psi_N>, <psi_N| H_zz |psi_N>
+    double e_num = 0.0, nrm2 = 0.0, ezz = 0.0;
+    set_h(h, h_target);
+    CKA(osmps_ed_energy(ed, x, &e_num, &nrm2));
+    *loss = e_num;
+    if (!want_grad) {
+        cleanup();
+        return OSMPS_OK;
+    }
+    set_h(h, 0.0);
+    CKA(osmps_ed_energy(ed, x, &ezz, &nrm2));
+
+    // ---- backward sweep ----
+    {
+        double Jr1[kMaxL];
+        for (int r = 1; r < h->L; ++r) Jr1[r - 1] = h->Jr[r];
+        CKA(osmps_ed_create(h->L, h->L > 1 ? Jr1 : nullptr, 0.0, -1.0, 0.0, h->prec, h->stream, &sib));
+        sib->h.reorth = h->reorth;
+    }
+    Handle *hb = &sib->h;
+    std::vector<double> xs(nquad), ws(nquad), gh(nsteps, 0.0);
+    gauss_legendre01(nquad, xs.data(), ws.data());
+    double gs = ezz;  // d/ds of <H_target> through its own coupling term
+    // lambda_N = H_target psi_N
+    set_h(h, h_target);
+    {
+        int np = 0;
+        HpsiArgs a{};
+        a.u = x;
+        a.out = lam;
+        a.tmp = h->tmp;
+        a.partials = h->partials;
+        a.epilogue = EPI_PLAIN;
+        CKAC(launch_hpsi(h, a, &np));
+    }
+    std::vector<double> zh(4 * nquad);
+    const int nseg = (nsteps + stride - 1) / stride;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int k0 = sgi * stride, k1 = std::min(nsteps, k0 + stride);
+        // psi_{k0} .. psi_{k1-1} of this segment, recomputed from its checkpoint
+        CKAC(cudaMemcpyAsync(seg[0], cp[sgi], vb, cudaMemcpyDeviceToDevice, h->stream));
+        for (int k = k0 + 1; k < k1; ++k) {
+            CKAC(cudaMemcpyAsync(seg[k - k0], seg[k - k0 - 1], vb, cudaMemcpyDeviceToDevice, h->stream));
+            CKA(step(seg[k - k0], h_steps[k - 1]));
+        }
+        for (int k = k1; k > k0; --k) {
+            const double hk = h_steps[k - 1];
+            void *psi_prev = seg[k - 1 - k0];
+            // Krylov bases of psi_{k-1} (handle h) and lambda_k (handle hb) under H(h_k)
+            set_h(h, hk);
+            set_h(hb, hk);
+            CKA(krylov_basis(h, psi_prev, m));
+            CKA(krylov_basis(hb, lam, m));
+            // Frechet derivative of exp(-i dt H) along X and along H_zz, by Gauss-Legendre in s:
+            //   <lambda_k| L(A, E) psi_{k-1}> = int_0^1 <e^{i s dt H} lambda_k| E |e^{-i (1-s) dt H} psi_{k-1}> ds
+            for (int q = 0; q < nquad; ++q) {
+                CKA(krylov_combine(h, m, (1.0 - xs[q]) * dt, ps));
+                CKA(krylov_combine(hb, m, -xs[q] * dt, ls));
+                int np = 0;
+                HpsiArgs a{};
+                a.u = ps;
+                a.tmp = h->tmp;
+                a.partials = h->partials;
+                a.epilogue = EPI_PLAIN;
+                set_h(h, 1.0);
+                a.out = w1;
+                CKAC(launch_hpsi(h, a, &np));  // H_zz ps + X ps
+                set_h(h, 0.0);
+                a.out = w0;
+                CKAC(launch_hpsi(h, a, &np));  // H_zz ps
+                CKAC(launch_cdot(h, ls, w1, zd + 4 * q));
+                CKAC(launch_cdot(h, ls, w0, zd + 4 * q + 2));
+            }
+            // lambda_{k-1} = exp(+i dt H(h_k)) lambda_k
+            CKA(krylov_combine(hb, m, -dt, lam));
+            CKAC(cudaMemcpyAsync(zh.data(), zd, sizeof(double) * 4 * nquad, cudaMemcpyDeviceToHost, h->stream));
+            CKAC(cudaStreamSynchronize(h->stream));
+            double gk = 0.0;
+            for (int q = 0; q < nquad; ++q) {
+                // d/dh_k: E = -i dt X, 2 Re(-i dt z) = 2 dt Im z with z = <ls| X ps> = z1 - z0
+                gk += ws[q] * 2.0 * dt * (zh[4 * q + 1] - zh[4 * q + 3]);
+                // d/ds: E = -i dt H_zz
+                gs += ws[q] * 2.0 * dt * zh[4 * q + 3];
+            }
+            gh[k - 1] = gk;
+        }
+    }
+    CKA(sync_and_check(h));
+    CKA(sync_and_check(hb));
+    if (grad_h != nullptr)
+        for (int k = 0; k < nsteps; ++k) grad_h[k] = gh[k];
+    if (grad_scale != nullptr) *grad_scale = gs;
+#undef CKA
+#undef CKAC
+    cleanup();
     return OSMPS_OK;
 }
 

@@ -89,6 +89,8 @@ int hpsi_partials_per_cta();
 // vec_kernels.cu
 cudaError_t launch_fill_basis(Handle *h, void *psi, uint64_t b);
 cudaError_t launch_norm2(Handle *h, const void *x, double *partials, int *nparts);
+// <a, b> = sum conj(a) b into out_dev[0..1] (re, im); uses partials2
+cudaError_t launch_cdot(Handle *h, const void *a, const void *b, double *out_dev);
 cudaError_t launch_ctl_after_norm(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j);
 cudaError_t launch_ctl_after_hpsi(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j);
 cudaError_t launch_update(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, double *partials,

@@ -112,6 +112,43 @@ __global__ void __launch_bounds__(kVecThreads) norm2_kernel(const typename VecT<
     block_reduce<1>(acc, partials + 4 * (size_t)blockIdx.x);
 }
 
+// partial <a, b> = sum conj(a_i) b_i (re, im) per CTA
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) cdot_kernel(const typename VecT<T>::v *a, const typename VecT<T>::v *b,
+                                                           uint64_t nvec, double *partials) {
+    typedef typename VecT<T>::v V;
+    constexpr int VE = VecT<T>::VE;
+    double acc[2] = {0.0, 0.0};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q0 < nvec; q0 += 4 * stride) {
+        T sr = 0, si = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint64_t q = q0 + r * stride;
+            if (q < nvec) {
+                const V x = a[q], y = b[q];
+#pragma unroll
+                for (int e = 0; e < VE; ++e) {
+                    sr = fma(re(x, e), re(y, e), fma(im(x, e), im(y, e), sr));
+                    si = fma(re(x, e), im(y, e), fma(-im(x, e), re(y, e), si));
+                }
+            }
+        }
+        acc[0] += (double)sr;
+        acc[1] += (double)si;
+    }
+    block_reduce<2>(acc, partials + 4 * (size_t)blockIdx.x);
+}
+
+__global__ void cdot_finish_kernel(const double *partials, int nparts, double *out) {
+    const double r = warp_sum_partials(partials, nparts, 4, 0);
+    const double i = warp_sum_partials(partials, nparts, 4, 1);
+    if (threadIdx.x == 0) {
+        out[0] = r;
+        out[1] = i;
+    }
+}
+
 // u_{j+1} = w - alpha_j scale_j u_j (in place on w) and partial |u_{j+1}|^2
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) update_kernel(typename VecT<T>::v *w, const typename VecT<T>::v *u,
@@ -629,6 +666,19 @@ cudaError_t launch_norm2(Handle *h, const void *x, double *partials, int *nparts
         norm2_kernel<float><<<g, kVecThreads, 0, h->stream>>>((const float4 *)x, nvec_of(h), partials);
     *nparts = g;
     h->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cdot(Handle *h, const void *a, const void *b, double *out_dev) {
+    const int g = vec_grid(h);
+    if (h->prec == OSMPS_FP64)
+        cdot_kernel<double><<<g, kVecThreads, 0, h->stream>>>((const double2 *)a, (const double2 *)b, nvec_of(h),
+                                                               h->partials2);
+    else
+        cdot_kernel<float><<<g, kVecThreads, 0, h->stream>>>((const float4 *)a, (const float4 *)b, nvec_of(h),
+                                                             h->partials2);
+    cdot_finish_kernel<<<1, 32, 0, h->stream>>>(h->partials2, g, out_dev);
+    h->launches += 2;
     return cudaGetLastError();
 }
 

@@ -314,3 +314,46 @@ def test_sparse_ground_energy_matches_jordan_wigner(L, h):
     Jr = O.coupling_table(L, 1.0, None)
     E_jw = O.jordan_wigner_ground_energy(L, 1.0, h)
     assert abs(O.ground_energy_sparse(L, Jr, h) - E_jw) < 1e-11 * abs(E_jw)
+
+
+# ---------------------------------------------------------------------------
+# final_energy_gradient_dense (reference gradients of the adjoint sweep)
+# ---------------------------------------------------------------------------
+
+def _fe_case(L=4, n=6, seed=41):
+    rng = np.random.Generator(np.random.Philox(seed))
+    return L, O.coupling_table(L, 1.0, 2.0), rng.uniform(0.5, 1.5, size=n), 0.07, si.basis_state(L, 0)
+
+
+def test_final_energy_gradient_matches_central_differences():
+    """Block-exponential (Frechet) gradients against central differences of the dense
+    expm forward model (a different path to the same derivative)."""
+    L, Jr, hs, dt, psi0 = _fe_case()
+    loss, gh, gs = O.final_energy_gradient_dense(L, Jr, hs, dt, 1.0, psi0)
+    eps = 1e-6
+    for k in range(len(hs)):
+        hp, hm = hs.copy(), hs.copy()
+        hp[k] += eps
+        hm[k] -= eps
+        fd = (O.final_energy_gradient_dense(L, Jr, hp, dt, 1.0, psi0)[0]
+              - O.final_energy_gradient_dense(L, Jr, hm, dt, 1.0, psi0)[0]) / (2 * eps)
+        assert abs(fd - gh[k]) < 1e-7 * max(1.0, abs(gh[k]))
+    fd = (O.final_energy_gradient_dense(L, (1 + eps) * Jr, hs, dt, 1.0, psi0)[0]
+          - O.final_energy_gradient_dense(L, (1 - eps) * Jr, hs, dt, 1.0, psi0)[0]) / (2 * eps)
+    assert abs(fd - gs) < 1e-7 * max(1.0, abs(gs))
+
+
+def test_final_energy_gradient_zero_field_closed_form():
+    """h_k = 0: the all-up state only acquires a phase, so loss = <up|H_zz|up> and
+    dloss/ds = sum_r (L - r) J(r) exactly."""
+    L = 5
+    Jr = O.coupling_table(L, 1.0, 1.5)
+    loss, gh, gs = O.final_energy_gradient_dense(L, Jr, np.zeros(4), 0.1, 1.0, si.basis_state(L, 0))
+    want = sum((L - r) * Jr[r - 1] for r in range(1, L))
+    assert abs(loss - want) < 1e-12 and abs(gs - want) < 1e-11
+
+
+def test_final_energy_krylov_matches_dense_loss():
+    L, Jr, hs, dt, psi0 = _fe_case(L=5, n=4, seed=43)
+    dense = O.final_energy_gradient_dense(L, Jr, hs, dt, 1.0, psi0)[0]
+    assert abs(O.final_energy_krylov(L, Jr, hs, dt, 20, 1.0, psi0) - dense) < 1e-11 * max(1.0, abs(dense))
