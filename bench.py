@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-hpsi28", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     return ap.parse_args()
 
 
@@ -356,6 +357,44 @@ def batched_ground(n=512, reps=3):
     return out
 
 
+def adjoint_L20(reps=2):
+    """Gradient of <H(h=1)> after 200 Krylov steps (dt = 0.025, m = 20) of the L = 20,
+    alpha = 2 chain with a seeded field h_k ~ U[0.5, 1.5], from all up: seconds per
+    gradient (loss, 200 field derivatives and the coupling-scale derivative), FP64 and
+    complex64.  H.psi products per gradient: forward N m, segment recomputation
+    <= N m, backward N (2 m + 2 nquad)."""
+    import numpy as np
+    import torch
+
+    import seeded_inputs as si
+    from paper_1802_10052_gb300 import Chain
+
+    L, n, dt, m, nq = 20, 200, 0.025, 20, 8
+    hs = si.field_schedule(n, seed=4)
+    out = {"workload": "H = sum |i-j|^-2 sz sz + h_k sum sx, L=20, 200 steps dt=0.025, m=20, h_k~U[0.5,1.5] "
+                       "(seed 4), loss <H(h=1)>, gradient w.r.t. all h_k and the coupling scale"}
+    products = n * m + n * m + n * (2 * m + 2 * nq)
+    for prec in ("fp64", "mixed"):
+        c = Chain(L, J=1.0, alpha=2.0, h=1.0, prec=prec)
+        x = c.new_state()
+        c.init_basis_state(x, 0)
+        c.adjoint_grad(x, hs, dt, m=m, nquad=nq)  # warm-up
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss, gh, gs = c.adjoint_grad(x, hs, dt, m=m, nquad=nq)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = min(ts)
+        esize = 16 if prec == "fp64" else 8
+        out[prec] = {"s_per_gradient": t, "loss": loss, "grad_scale": gs, "grad_h_norm": float(np.linalg.norm(gh)),
+                     "hpsi_products": products,
+                     "algorithmic_GBps_of_products": products * 2.0 * (1 << L) * esize / t / 1e9}
+        c.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -472,6 +511,8 @@ def main():
         extra["hpsi_L28"] = [hpsi_L28("mixed"), hpsi_L28("fp64", reps=6)]
     if rank == 0 and not args.no_batch:
         extra["batched_ground_512"] = batched_ground()
+    if rank == 0 and not args.no_grad:
+        extra["adjoint_grad_L20"] = adjoint_L20()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_line()
