@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--profile-case", choices=["batch_L16"], default=None,
+                    help="run one small profiling workload and exit (for ncu captures)")
     return ap.parse_args()
 
 
@@ -491,8 +493,33 @@ def cpu_baseline_line():
                       f"Krylov steps of m=20 and 10 measurement sets per unit time"}
 
 
+def profile_case(name):
+    """Small workloads sized for full ncu captures (a few hundred MB on the device)."""
+    import numpy as np
+    import torch
+
+    import seeded_inputs as si
+    from paper_1802_10052_gb300 import ChainBatch
+
+    torch.cuda.set_device(0)
+    if name == "batch_L16":
+        # 152 chains of L = 16 (one per SM), alpha = 1.7, h = 0.9, seeded Gaussian starts; two solves
+        n, L = 152, 16
+        b = ChainBatch([L] * n, [1.0] * n, [1.7] * n, [0.9] * n, prec="mixed", max_iter=1000)
+        start = torch.from_numpy(np.concatenate([v.astype(np.complex64)
+                                                 for v in si.batch_start_states([L] * n, seed=3)])).cuda()
+        psi = start.clone()
+        for _ in range(2):
+            psi.copy_(start)
+            b.lanczos_ground(psi, 1e-10)
+        print(json.dumps({"profile_case": name, "iters_mean": float(b.iters.float().mean())}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case is not None:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     import torch
