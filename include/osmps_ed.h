@@ -335,6 +335,29 @@ osmps_status osmps_ed_batch_lanczos_ground(osmps_ed_batch_t *b, void *psi, doubl
 osmps_status osmps_ed_batch_check(osmps_ed_batch_t *b);
 osmps_status osmps_ed_batch_launch_count(const osmps_ed_batch_t *b, int64_t *count);
 
+/*
+ * Two-site gates (quantum cellular automata and gates, App. C): applies the
+ * ngates 4 x 4 complex matrices U[32 i .. 32 i + 31] (row-major, (re, im)
+ * interleaved, basis index 2 sigma_s + sigma_{s+1} with sigma = 0 for up) to
+ * the bonds (site[i], site[i] + 1), 1 <= site[i] <= L-1, in place.  The bonds
+ * must be pairwise disjoint (one layer; the gates then commute).  Gates need
+ * not be unitary.  Requires L >= 4 (EUNSUPPORTED otherwise).  Enqueues only.
+ */
+osmps_status osmps_ed_apply_gates(osmps_ed_t *ed, void *psi, int ngates, const int *site, const double *U);
+
+/*
+ * psi <- (Trotter product)^nsteps psi for a nearest-neighbour chain (Sec.
+ * III.C): H = H_o + H_e, the bonds (s, s+1) with s odd and with s even, each
+ * site field weighted 1/2 in each layer (the first and last site 1, open
+ * chain); the layer exponentials are exact two-site propagators.
+ *   order 1  Eq. trotter1: exp(-i dt H_o) exp(-i dt H_e)
+ *   order 2  Eq. trotter2: exp(-i dt/2 H_e) exp(-i dt H_o) exp(-i dt/2 H_e)
+ *   order 4  Eqs. trotter4, trotter4c (eleven layers per step).
+ * EUNSUPPORTED for couplings beyond the nearest neighbour or L < 4.
+ * Enqueues only.
+ */
+osmps_status osmps_ed_trotter_evolve(osmps_ed_t *ed, void *psi, double dt, int nsteps, int order);
+
 /* Static description of a status code. */
 const char *osmps_ed_strerror(osmps_status status);
 

@@ -345,6 +345,79 @@ def evolve(make_matvec, psi0: np.ndarray, dt: float, nsteps: int, m: int, field_
 
 
 # ---------------------------------------------------------------------------
+# Trotter decomposition for nearest-neighbour chains (Sec. III.C) and
+# two-site gates on the rank-L tensor (Fig. of the tensor operations; App. C)
+# ---------------------------------------------------------------------------
+
+def apply_two_site(psi: np.ndarray, L: int, site: int, U: np.ndarray) -> np.ndarray:
+    """Contract a 4 x 4 operator (basis index 2 sigma_s + sigma_{s+1}) with the two
+    indices of sites (s, s+1) of psi viewed as a rank-L tensor (site 1 first),
+    the tensordot route of Sec. III.C."""
+    T = np.asarray(psi, dtype=np.complex128).reshape((2,) * L)
+    G = np.asarray(U, dtype=np.complex128).reshape(2, 2, 2, 2)  # (out_s, out_s1, in_s, in_s1)
+    T = np.tensordot(G, T, axes=([2, 3], [site - 1, site]))  # new axes 0, 1 = sites s, s+1 first
+    T = np.moveaxis(T, [0, 1], [site - 1, site])
+    return T.reshape(-1)
+
+
+def bond_terms(L: int, J1: float, h):
+    """Two-site terms h_(s,s+1) = J1 sz sz + w_s h_s sx(x)1 + w_{s+1} h_{s+1} 1(x)sx with site
+    weights 1/2 (1 for the first and last site): H = sum_s h_(s,s+1) (Sec. III.C)."""
+    hk = site_fields(L, h)
+    terms = {}
+    for s in range(1, L):
+        ws = 1.0 if s == 1 else 0.5
+        ws1 = 1.0 if s + 1 == L else 0.5
+        terms[s] = J1 * np.kron(SZ, SZ) + ws * hk[s - 1] * np.kron(SX, I2) + ws1 * hk[s] * np.kron(I2, SX)
+    return terms
+
+
+def trotter_factors(order: int):
+    """(parity, fraction of dt) of the layers of one step, applied first to last:
+    parity 0 = H_e (bonds from even sites), 1 = H_o.  Eqs. trotter1, trotter2, trotter4/4c."""
+    if order == 1:
+        return [(0, 1.0), (1, 1.0)]
+    if order == 2:
+        return [(0, 0.5), (1, 1.0), (0, 0.5)]
+    t3 = 1.0 / (2.0 * (4.0 - 4.0 ** (1.0 / 3.0)))
+    t1, t2, t4 = 1.0 - 8.0 * t3, 0.5 * (1.0 - 6.0 * t3), 2.0 * t3
+    seq = [t3, t4, t4, t4, t2, t1, t2, t4, t4, t4, t3]
+    return [(1 if f % 2 else 0, x) for f, x in enumerate(seq)]
+
+
+def trotter_evolve_tensor(psi: np.ndarray, L: int, J1: float, h, dt: float, nsteps: int, order: int) -> np.ndarray:
+    """Trotter evolution by two-site propagators expm(-i tau h_bond) applied on the tensor."""
+    terms = bond_terms(L, J1, h)
+    psi = np.asarray(psi, dtype=np.complex128)
+    cache = {}
+    for _ in range(nsteps):
+        for parity, frac in trotter_factors(order):
+            for s in range(1, L):
+                if s % 2 != parity:
+                    continue
+                key = (s, frac)
+                if key not in cache:
+                    cache[key] = sla.expm(-1j * frac * dt * terms[s])
+                psi = apply_two_site(psi, L, s, cache[key])
+    return psi
+
+
+def trotter_evolve_dense(psi: np.ndarray, L: int, J1: float, h, dt: float, nsteps: int, order: int) -> np.ndarray:
+    """The same product from the dense layer Hamiltonians H_o, H_e built by Kronecker
+    products (small L)."""
+    terms = bond_terms(L, J1, h)
+    D = 1 << L
+    Hp = [np.zeros((D, D)), np.zeros((D, D))]
+    for s, t in terms.items():
+        Hp[s % 2] += np.kron(np.kron(np.eye(1 << (s - 1)), t), np.eye(1 << (L - s - 1)))
+    psi = np.asarray(psi, dtype=np.complex128)
+    for _ in range(nsteps):
+        for parity, frac in trotter_factors(order):
+            psi = sla.expm(-1j * frac * dt * Hp[parity]) @ psi
+    return psi
+
+
+# ---------------------------------------------------------------------------
 # Gradient of a final energy under a piecewise-constant field (the paper has
 # no gradients: the derivative of its Krylov/expm time evolution, Sec. III.D)
 # ---------------------------------------------------------------------------

@@ -188,6 +188,23 @@ class Chain:
               "osmps_ed_adjoint_grad")
         return (loss.value, gh, gs.value) if want_grad else (loss.value, None, None)
 
+    def apply_gates(self, psi, sites, U):
+        """In place: apply 4 x 4 gates U[i] (complex, basis 2 sigma_s + sigma_{s+1}) on the
+        disjoint bonds (sites[i], sites[i] + 1)."""
+        self._check_state(psi)
+        sites = [int(x) for x in sites]
+        n = len(sites)
+        Ua = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).reshape(n, 4, 4)).view(np.float64).ravel()
+        sa = (C.c_int * max(n, 1))(*sites)
+        check(lib.osmps_ed_apply_gates(self._h, _dptr(psi), n, sa, Ua.ctypes.data_as(C.POINTER(C.c_double))),
+              "osmps_ed_apply_gates")
+
+    def trotter_evolve(self, psi, dt, nsteps, order=2):
+        """In place: psi <- Trotter product (order 1, 2 or 4) of exp(-i H dt), nsteps times."""
+        self._check_state(psi)
+        check(lib.osmps_ed_trotter_evolve(self._h, _dptr(psi), float(dt), int(nsteps), int(order)),
+              "osmps_ed_trotter_evolve")
+
     def measure_local(self, psi):
         self._check_state(psi)
         out = np.zeros(self.L)

@@ -932,4 +932,60 @@ osmps_status osmps_ed_adjoint_grad(osmps_ed_t *ed, const void *psi0, int nsteps,
     return OSMPS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Two-site gates and Trotter evolution (see include/osmps_ed.h)
+// ---------------------------------------------------------------------------
+osmps_status osmps_ed_apply_gates(osmps_ed_t *ed, void *psi, int ngates, const int *site, const double *U) {
+    if (ed == nullptr || ngates < 0 || (ngates > 0 && (site == nullptr || U == nullptr))) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    const int L = h->L;
+    if (L < 4) return OSMPS_EUNSUPPORTED;
+    std::vector<char> used(L + 2, 0);
+    std::vector<int> lo(ngates);
+    for (int i = 0; i < ngates; ++i) {
+        const int s = site[i];
+        if (s < 1 || s > L - 1 || used[s] || used[s + 1]) return OSMPS_EINVAL;  // bonds must be disjoint
+        used[s] = used[s + 1] = 1;
+        for (int e = 0; e < 32; ++e)
+            if (!std::isfinite(U[32 * i + e])) return OSMPS_EINVAL;
+        lo[i] = L - s - 1;
+    }
+    if (ngates == 0) return OSMPS_OK;
+    CK(gates::launch_gate_layer(h, psi, ngates, lo.data(), U));
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_trotter_evolve(osmps_ed_t *ed, void *psi, double dt, int nsteps, int order) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    if (!std::isfinite(dt) || nsteps < 0 || (order != 1 && order != 2 && order != 4)) return OSMPS_EINVAL;
+    if (h->L < 4) return OSMPS_EUNSUPPORTED;
+    for (int r = 2; r < h->L; ++r)
+        if (h->Jr[r] != 0.0) return OSMPS_EUNSUPPORTED;  // nearest-neighbour chains only
+    if (nsteps == 0) return OSMPS_OK;
+    auto E = [&](double tau) { return gates::trotter_layer(h, psi, 0, tau); };
+    auto O = [&](double tau) { return gates::trotter_layer(h, psi, 1, tau); };
+    if (order == 1) {  // Eq. trotter1: exp(-i dt H_o) exp(-i dt H_e)
+        for (int k = 0; k < nsteps; ++k) {
+            CK(E(dt));
+            CK(O(dt));
+        }
+    } else if (order == 2) {  // Eq. trotter2, the half steps of neighbouring steps merged
+        CK(E(0.5 * dt));
+        for (int k = 0; k < nsteps; ++k) {
+            CK(O(dt));
+            CK(E(k + 1 < nsteps ? dt : 0.5 * dt));
+        }
+    } else {  // Eqs. trotter4, trotter4c
+        const double t3 = 1.0 / (2.0 * (4.0 - std::cbrt(4.0)));
+        const double t1 = 1.0 - 8.0 * t3, t2 = 0.5 * (1.0 - 6.0 * t3), t4 = 2.0 * t3;
+        const double seq[11] = {t3, t4, t4, t4, t2, t1, t2, t4, t4, t4, t3};  // E, O, E, ... from the right
+        for (int k = 0; k < nsteps; ++k)
+            for (int f = 0; f < 11; ++f) CK((f & 1) ? O(seq[f] * dt) : E(seq[f] * dt));
+    }
+    return OSMPS_OK;
+}
+
 }  // extern "C"

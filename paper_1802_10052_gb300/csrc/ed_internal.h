@@ -173,6 +173,14 @@ struct Handle {
 void *dev_alloc(Handle *h, size_t bytes, cudaError_t *err);
 void dev_free(Handle *h, void *p, size_t bytes);
 
+// two-site gates (gate_kernels.cu)
+namespace gates {
+// gate i on bits (lo[i] + 1, lo[i]): U[32 i ..] 4 x 4 complex, row-major, basis 2 bit_hi + bit_lo
+cudaError_t launch_gate_layer(Handle *h, void *psi, int ng, const int *lo, const double *U);
+// exp(-i tau H_p) psi, p = 1: bonds (s, s+1) with s odd (H_o), p = 0: s even (H_e)
+cudaError_t trotter_layer(Handle *h, void *psi, int parity, double tau);
+}  // namespace gates
+
 // ---------------------------------------------------------------------------
 // Batched ground states (batch_kernels.cu, batch_api.cu)
 // ---------------------------------------------------------------------------

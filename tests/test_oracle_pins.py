@@ -357,3 +357,55 @@ def test_final_energy_krylov_matches_dense_loss():
     L, Jr, hs, dt, psi0 = _fe_case(L=5, n=4, seed=43)
     dense = O.final_energy_gradient_dense(L, Jr, hs, dt, 1.0, psi0)[0]
     assert abs(O.final_energy_krylov(L, Jr, hs, dt, 20, 1.0, psi0) - dense) < 1e-11 * max(1.0, abs(dense))
+
+
+# ---------------------------------------------------------------------------
+# Trotter decomposition and two-site gates (Sec. III.C, App. C)
+# ---------------------------------------------------------------------------
+
+def test_two_site_contraction_matches_kronecker_embedding():
+    L = 5
+    rng = np.random.Generator(np.random.Philox(51))
+    psi = si.gaussian_state(L, 52)
+    U = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    for s in range(1, L):
+        full = np.kron(np.kron(np.eye(1 << (s - 1)), U), np.eye(1 << (L - s - 1)))
+        np.testing.assert_allclose(O.apply_two_site(psi, L, s, U), full @ psi, atol=1e-13)
+
+
+@pytest.mark.parametrize("order", [1, 2, 4])
+def test_trotter_tensor_matches_dense_layers(order):
+    L = 6
+    psi = si.gaussian_state(L, 53)
+    a = O.trotter_evolve_tensor(psi, L, 1.0, 0.7, 0.1, 3, order)
+    b = O.trotter_evolve_dense(psi, L, 1.0, 0.7, 0.1, 3, order)
+    assert np.linalg.norm(a - b) < 1e-12
+
+
+def test_trotter_sum_of_layers_is_the_hamiltonian():
+    """sum of bond terms with the 1/2 (1 at the ends) site weights = H of Eq. HQI."""
+    L = 6
+    terms = O.bond_terms(L, -1.0, -0.8)
+    H = sum(np.kron(np.kron(np.eye(1 << (s - 1)), t), np.eye(1 << (L - s - 1))) for s, t in terms.items())
+    np.testing.assert_allclose(H, O.hamiltonian_dense(L, O.coupling_table(L, -1.0, None), -0.8), atol=1e-13)
+
+
+def test_trotter_exact_without_bonds():
+    """J = 0: all layer terms commute, so every order is exact."""
+    L = 6
+    psi = si.gaussian_state(L, 54)
+    exact = O.exact_propagate_dense(O.hamiltonian_dense(L, O.coupling_table(L, 0.0, None), 0.9), psi, 0.5)
+    for order in (1, 2, 4):
+        assert np.linalg.norm(O.trotter_evolve_tensor(psi, L, 0.0, 0.9, 0.1, 5, order) - exact) < 1e-12
+
+
+@pytest.mark.parametrize("order,rate", [(1, 1.0), (2, 2.0), (4, 4.0)])
+def test_trotter_convergence_order(order, rate):
+    """Global error at fixed t falls like dt^order (Sec. V convergence studies)."""
+    L, t = 8, 0.8
+    psi = si.gaussian_state(L, 55)
+    exact = O.exact_propagate_dense(O.hamiltonian_dense(L, O.coupling_table(L, 1.0, None), 0.6), psi, t)
+    errs = []
+    for n in (8, 16):
+        errs.append(np.linalg.norm(O.trotter_evolve_tensor(psi, L, 1.0, 0.6, t / n, n, order) - exact))
+    assert abs(math.log2(errs[0] / errs[1]) - rate) < 0.25
