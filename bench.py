@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-trotter", action="store_true")
     ap.add_argument("--profile-case", choices=["batch_L16"], default=None,
                     help="run one small profiling workload and exit (for ncu captures)")
     return ap.parse_args()
@@ -397,6 +398,46 @@ def adjoint_L20(reps=2):
     return out
 
 
+def trotter_nn(L=24, reps=10):
+    """Nearest-neighbour chain (J = 1, h = 1, open, complex64): ms per time step of the
+    Trotter products of order 2 and 4 (Sec. III.C) against one Krylov step (m = 20) on the
+    same chain, both timed with CUDA events.  Bytes per step: every window pass reads and
+    writes the state once (2 D s); order 2 = 2 layers, order 4 = 11 layers per step, a layer
+    = ceil(bonds / 2) window passes."""
+    import torch
+
+    from paper_1802_10052_gb300 import Chain
+
+    c = Chain(L, couplings=[1.0] + [0.0] * (L - 2), h=1.0, prec="mixed")
+    x = c.new_state()
+    c.init_basis_state(x, 0)
+    out = {"workload": f"NN transverse Ising L={L}, J=1, h=1, open, dt=0.01, complex64"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    D = 1 << L
+    passes_per_layer = {0: ((L - 1) // 2 + 1) // 2, 1: (L // 2 + 1) // 2}
+    for order, layers in ((2, [(0, 1), (1, 1)]), (4, [(f % 2, 1) for f in range(11)])):
+        c.trotter_evolve(x, 0.01, 2, order)
+        torch.cuda.synchronize()
+        e0.record()
+        c.trotter_evolve(x, 0.01, reps, order)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        npass = sum(passes_per_layer[p] for p, _ in layers)
+        out[f"order{order}"] = {"ms_per_step": ms, "window_passes_per_step": npass,
+                                "GBps": npass * 2.0 * D * 8 / (ms * 1e-3) / 1e9}
+    c.krylov_evolve(x, 0.01, 1, 20)
+    torch.cuda.synchronize()
+    e0.record()
+    c.krylov_evolve(x, 0.01, 3, 20)
+    e1.record()
+    torch.cuda.synchronize()
+    out["krylov_m20_ms_per_step"] = e0.elapsed_time(e1) / 3
+    out["krylov_over_trotter2"] = out["krylov_m20_ms_per_step"] / out["order2"]["ms_per_step"]
+    c.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -540,6 +581,8 @@ def main():
         extra["batched_ground_512"] = batched_ground()
     if rank == 0 and not args.no_grad:
         extra["adjoint_grad_L20"] = adjoint_L20()
+    if rank == 0 and not args.no_trotter:
+        extra["trotter_nn_L24"] = trotter_nn()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_line()
