@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-trotter", action="store_true")
+    ap.add_argument("--no-rdm", action="store_true")
     ap.add_argument("--profile-case", choices=["batch_L16"], default=None,
                     help="run one small profiling workload and exit (for ncu captures)")
     return ap.parse_args()
@@ -438,6 +439,38 @@ def trotter_nn(L=24, reps=10):
     return out
 
 
+def rdm_L24(reps=3):
+    """All 276 two-site RDMs and the bond entropy of all 23 cuts of an L = 24 complex64
+    state (the quench state after 0.2 time units): ms per call.  The pair kernel reads
+    the state once per pair: 276 x D x 8 B."""
+    import torch
+
+    from paper_1802_10052_gb300 import Chain
+
+    L = 24
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    x = c.new_state()
+    c.init_basis_state(x, 0)
+    c.krylov_evolve(x, 0.01, 20, 20)
+    c.rdm_pairs(x)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.rdm_pairs(x)
+        ts.append(time.perf_counter() - t0)
+    t_rdm = min(ts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c.entropy_sweep(x)
+    t_sweep = time.perf_counter() - t0
+    npairs = L * (L - 1) // 2
+    c.close()
+    return {"workload": "L=24 complex64 state, all pairs (276) and all cuts (23)",
+            "rdm_pairs_ms": t_rdm * 1e3, "rdm_GBps": npairs * (1 << L) * 8 / t_rdm / 1e9,
+            "entropy_sweep_ms": t_sweep * 1e3}
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -583,6 +616,8 @@ def main():
         extra["adjoint_grad_L20"] = adjoint_L20()
     if rank == 0 and not args.no_trotter:
         extra["trotter_nn_L24"] = trotter_nn()
+    if rank == 0 and not args.no_rdm:
+        extra["rdm_L24"] = rdm_L24()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_line()

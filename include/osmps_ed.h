@@ -358,6 +358,25 @@ osmps_status osmps_ed_apply_gates(osmps_ed_t *ed, void *psi, int ngates, const i
  */
 osmps_status osmps_ed_trotter_evolve(osmps_ed_t *ed, void *psi, double dt, int nsteps, int order);
 
+/*
+ * Reduced density matrices of every pair of sites (Sec. IV: trace out the
+ * other L-2 indices of the rank-L tensor), i.e. all two-point Pauli
+ * correlators <s^a_i s^b_j> = Tr(s^a (x) s^b rho_ij):
+ *     rho_ij[v'][v] = sum_rest psi(v', rest) conj(psi(v, rest)),  v = 2 sigma_i + sigma_j
+ * (sigma = 0 for up).  rdm2: host, L(L-1)/2 matrices of 4 x 4 complex ((re, im),
+ * row-major), pairs ordered (1,2), (1,3), ..., (1,L), (2,3), ..., (L-1,L); or NULL.
+ * rdm1: host, L matrices of 2 x 2 complex (the one-site RDMs, partial traces of
+ * the pair RDMs); or NULL.  L >= 2.  FP64 reductions.  Allocates its scratch
+ * for the call.  Synchronises.
+ */
+osmps_status osmps_ed_rdm_pairs(osmps_ed_t *ed, const void *psi, double *rdm2, double *rdm1);
+
+/*
+ * Bond entropy of every cut: S[l-1] = S(sites 1..l | l+1..L) for l = 1..L-1
+ * (Sec. IV bond entropy, Sec. V), each as osmps_ed_schmidt_entropy.  Synchronises.
+ */
+osmps_status osmps_ed_entropy_sweep(osmps_ed_t *ed, const void *psi, double *S);
+
 /* Static description of a status code. */
 const char *osmps_ed_strerror(osmps_status status);
 

@@ -205,6 +205,26 @@ class Chain:
         check(lib.osmps_ed_trotter_evolve(self._h, _dptr(psi), float(dt), int(nsteps), int(order)),
               "osmps_ed_trotter_evolve")
 
+    def rdm_pairs(self, psi):
+        """(rho2, rho1): rho2[p] the 4 x 4 RDM of the p-th pair (1,2), (1,3), ..., (L-1,L)
+        in the basis 2 sigma_i + sigma_j; rho1[i] the 2 x 2 RDM of site i+1."""
+        self._check_state(psi)
+        L = self.L
+        npairs = L * (L - 1) // 2
+        r2 = np.zeros(npairs * 32)
+        r1 = np.zeros(L * 8)
+        check(lib.osmps_ed_rdm_pairs(self._h, _dptr(psi), r2.ctypes.data_as(C.POINTER(C.c_double)),
+                                     r1.ctypes.data_as(C.POINTER(C.c_double))), "osmps_ed_rdm_pairs")
+        return r2.view(np.complex128).reshape(npairs, 4, 4), r1.view(np.complex128).reshape(L, 2, 2)
+
+    def entropy_sweep(self, psi):
+        """Bond entropy S(l) of every cut l = 1..L-1."""
+        self._check_state(psi)
+        S = np.zeros(self.L - 1)
+        check(lib.osmps_ed_entropy_sweep(self._h, _dptr(psi), S.ctypes.data_as(C.POINTER(C.c_double))),
+              "osmps_ed_entropy_sweep")
+        return S
+
     def measure_local(self, psi):
         self._check_state(psi)
         out = np.zeros(self.L)

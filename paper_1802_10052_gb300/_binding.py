@@ -42,6 +42,8 @@ SIGNATURES = {
     "osmps_ed_adjoint_grad": (_I, [_P, _P, _I, _D, _DP, _I, _D, _I, _I, _DP, _DP, _DP]),
     "osmps_ed_apply_gates": (_I, [_P, _P, _I, C.POINTER(_I), _DP]),
     "osmps_ed_trotter_evolve": (_I, [_P, _P, _D, _I, _I]),
+    "osmps_ed_rdm_pairs": (_I, [_P, _P, _DP, _DP]),
+    "osmps_ed_entropy_sweep": (_I, [_P, _P, _DP]),
     "osmps_ed_measure_local": (_I, [_P, _P, _DP]),
     "osmps_ed_measure_corr": (_I, [_P, _P, _DP]),
     "osmps_ed_measure_zz": (_I, [_P, _P, _DP, _DP]),

@@ -988,4 +988,74 @@ osmps_status osmps_ed_trotter_evolve(osmps_ed_t *ed, void *psi, double dt, int n
     return OSMPS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Reduced density matrices of all pairs and the bond-entropy sweep
+// ---------------------------------------------------------------------------
+osmps_status osmps_ed_rdm_pairs(osmps_ed_t *ed, const void *psi, double *rdm2, double *rdm1) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    const int L = h->L;
+    if (L < 2) return OSMPS_EINVAL;
+    const int npairs = L * (L - 1) / 2;
+    double *scr = nullptr;
+    const size_t nd = pair_rdm_scratch_doubles(L);
+    if (cudaMalloc(&scr, sizeof(double) * nd) != cudaSuccess) {
+        cudaGetLastError();
+        return OSMPS_ENOMEM;
+    }
+    double *out_dev = scr + (nd - (size_t)npairs * 16);
+    std::vector<double> vals((size_t)npairs * 16);
+    cudaError_t err = launch_pair_rdm(h, psi, scr, out_dev);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(vals.data(), out_dev, sizeof(double) * vals.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    cudaFree(scr);
+    CK(err);
+    // assemble the Hermitian 4 x 4 matrices, (re, im) row-major
+    std::vector<double> R((size_t)npairs * 32, 0.0);
+    for (int p = 0; p < npairs; ++p) {
+        const double *v = &vals[(size_t)p * 16];
+        double *M = &R[(size_t)p * 32];
+        for (int d = 0; d < 4; ++d) M[(d * 4 + d) * 2] = v[d];
+        int q = 4;
+        for (int v1 = 0; v1 < 4; ++v1)
+            for (int v2 = v1 + 1; v2 < 4; ++v2) {
+                M[(v1 * 4 + v2) * 2] = v[q];
+                M[(v1 * 4 + v2) * 2 + 1] = v[q + 1];
+                M[(v2 * 4 + v1) * 2] = v[q];
+                M[(v2 * 4 + v1) * 2 + 1] = -v[q + 1];
+                q += 2;
+            }
+    }
+    if (rdm2 != nullptr) std::memcpy(rdm2, R.data(), sizeof(double) * R.size());
+    if (rdm1 != nullptr) {
+        // rho_i = Tr_j rho_ij with the pair (i, i+1) (the last site from (L-1, L))
+        auto pidx = [&](int i, int j) { return (i - 1) * L - (i - 1) * i / 2 + (j - i - 1); };
+        for (int i = 1; i <= L; ++i) {
+            const bool first = i < L;
+            const double *M = &R[(size_t)(first ? pidx(i, i + 1) : pidx(L - 1, L)) * 32];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    double re = 0.0, im = 0.0;
+                    for (int t = 0; t < 2; ++t) {
+                        const int r = first ? 2 * a + t : 2 * t + a, c = first ? 2 * b + t : 2 * t + b;
+                        re += M[(r * 4 + c) * 2];
+                        im += M[(r * 4 + c) * 2 + 1];
+                    }
+                    rdm1[(size_t)(i - 1) * 8 + (a * 2 + b) * 2] = re;
+                    rdm1[(size_t)(i - 1) * 8 + (a * 2 + b) * 2 + 1] = im;
+                }
+        }
+    }
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_entropy_sweep(osmps_ed_t *ed, const void *psi, double *S) {
+    if (ed == nullptr || S == nullptr) return OSMPS_EINVAL;
+    if (ed->h.L < 2) return OSMPS_EINVAL;
+    for (int cut = 1; cut < ed->h.L; ++cut) CKS(osmps_ed_schmidt_entropy(ed, psi, cut, nullptr, &S[cut - 1]));
+    return OSMPS_OK;
+}
+
 }  // extern "C"

@@ -173,6 +173,10 @@ struct Handle {
 void *dev_alloc(Handle *h, size_t bytes, cudaError_t *err);
 void dev_free(Handle *h, void *p, size_t bytes);
 
+// reduced density matrices of all pairs (rdm_kernels.cu): 16 reals per pair into out_dev
+cudaError_t launch_pair_rdm(Handle *h, const void *psi, double *scratch_dev, double *out_dev);
+size_t pair_rdm_scratch_doubles(int L);  // scratch plus the npairs x 16 output at its end
+
 // two-site gates (gate_kernels.cu)
 namespace gates {
 // gate i on bits (lo[i] + 1, lo[i]): U[32 i ..] 4 x 4 complex, row-major, basis 2 bit_hi + bit_lo

@@ -409,3 +409,42 @@ def test_trotter_convergence_order(order, rate):
     for n in (8, 16):
         errs.append(np.linalg.norm(O.trotter_evolve_tensor(psi, L, 1.0, 0.6, t / n, n, order) - exact))
     assert abs(math.log2(errs[0] / errs[1]) - rate) < 0.25
+
+
+# ---------------------------------------------------------------------------
+# two-site reduced density matrices (references of the all-pairs RDM kernel)
+# ---------------------------------------------------------------------------
+
+def test_pair_rdm_closed_forms():
+    """Product state: rho_ij = |a_i><a_i| (x) |a_j><a_j|; GHZ: (|00><00| + |11><11|)/2;
+    a Bell pair on sites (2, 4) of a product state: the Bell projector."""
+    L = 5
+    b = si.neel_index(L)
+    psi = si.basis_state(L, b)
+    bits = [(b >> (L - s)) & 1 for s in range(1, L + 1)]
+    for i, j in ((1, 2), (2, 5), (3, 4)):
+        want = np.zeros((4, 4))
+        v = 2 * bits[i - 1] + bits[j - 1]
+        want[v, v] = 1.0
+        np.testing.assert_allclose(O.rdm_sites(psi, L, (i, j)), want, atol=1e-15)
+    g = si.ghz_state(L)
+    np.testing.assert_allclose(O.rdm_sites(g, L, (1, 4)), np.diag([0.5, 0, 0, 0.5]), atol=1e-15)
+    bell = np.zeros(1 << L, dtype=np.complex128)
+    bell[0] = 1 / math.sqrt(2)                               # sites 2, 4 both up
+    bell[(1 << (L - 2)) | (1 << (L - 4))] = 1j / math.sqrt(2)  # sites 2, 4 both down
+    want = np.zeros((4, 4), dtype=np.complex128)
+    want[0, 0] = want[3, 3] = 0.5
+    want[0, 3] = -0.5j
+    want[3, 0] = 0.5j
+    np.testing.assert_allclose(O.rdm_sites(bell, L, (2, 4)), want, atol=1e-15)
+
+
+def test_pair_rdm_partial_trace_and_positivity():
+    L = 6
+    psi = si.gaussian_state(L, 81)
+    r = O.rdm_sites(psi, L, (2, 5))
+    assert abs(np.trace(r) - 1.0) < 1e-13
+    np.testing.assert_allclose(r, r.conj().T, atol=1e-15)
+    assert np.linalg.eigvalsh(r).min() > -1e-14
+    tr_j = r.reshape(2, 2, 2, 2).trace(axis1=1, axis2=3)
+    np.testing.assert_allclose(tr_j, O.rdm_sites(psi, L, (2,)), atol=1e-14)
