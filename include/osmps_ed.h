@@ -114,6 +114,13 @@ osmps_status osmps_ed_set_reorth(osmps_ed_t *ed, int mode);
  * not apply).  Not from the paper (implementation choice). */
 osmps_status osmps_ed_set_gram_mode(osmps_ed_t *ed, int mode);
 
+/* Number of SMs the handle's kernels size their grids for (persistent
+ * kernels launch one CTA per SM of this count): 1..device SMs, 0 = all.
+ * A smaller count leaves SMs free for work on other streams, e.g. the
+ * eigen-solves of osmps_ed_schmidt_entropy_async.  Not from the paper
+ * (scheduling). */
+osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm);
+
 /* D = 2^L. */
 osmps_status osmps_ed_dim(const osmps_ed_t *ed, uint64_t *D);
 
@@ -260,6 +267,30 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
                                       double *S);
 
 /*
+ * The same measurement without blocking the caller (Sec. IV, entanglement
+ * measures taken along a time evolution).  The Gram product rho =
+ * psi_A psi_A^dag is enqueued on the handle's stream, so psi may be changed
+ * by work enqueued after this call; the eigen-solve and the entropy then run
+ * on a lowest-priority non-blocking stream of the handle, driven by a worker
+ * thread of the handle (the eigen-solver blocks its host thread).  Results go
+ * to the host pointers S (one double) and lambda (2^min(cut, L-cut) doubles,
+ * or NULL), which the caller keeps valid and does not read until
+ * osmps_ed_measure_wait returns.  Two measurements may be outstanding; a
+ * third call blocks the caller until the older one has finished.  Buffers of
+ * the asynchronous path are not counted by osmps_ed_device_bytes.  Errors of
+ * the argument checks and of the Gram product return here; errors of the
+ * eigen-solve are returned by the next osmps_ed_measure_wait.  Not from the
+ * paper (scheduling).
+ */
+osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int cut, double *S,
+                                            double *lambda);
+
+/* Blocks until every osmps_ed_schmidt_entropy_async of this handle has
+ * written its results; returns the first error among them (then clears it).
+ * Call it before osmps_ed_destroy when measurements are outstanding. */
+osmps_status osmps_ed_measure_wait(osmps_ed_t *ed);
+
+/*
  * Timing of the H.psi products with CUDA events recorded on the handle's
  * stream around every product (all passes), for roofline measurements.
  * Not from the paper (instrumentation).  enable = 0 stops recording.
@@ -271,7 +302,8 @@ osmps_status osmps_ed_timing_enable(osmps_ed_t *ed, int enable);
 osmps_status osmps_ed_timing_read(osmps_ed_t *ed, double *hpsi_ms, int64_t *hpsi_calls, int reset);
 
 /* Number of kernels this handle has launched so far (its own kernels; the
- * cuSOLVER eigenvalue routine is not counted).  Not from the paper. */
+ * cuSOLVER eigenvalue routine is not counted; those of the asynchronous
+ * entropy are added at osmps_ed_measure_wait).  Not from the paper. */
 osmps_status osmps_ed_launch_count(const osmps_ed_t *ed, int64_t *count);
 
 /*

@@ -20,7 +20,7 @@ import numpy as np
 
 from ._binding import (LIB_PATH, OSMPS_ENOCONV, OSMPS_FP64, OSMPS_MIXED, OSMPS_OK, OsmpsError, check, lib)
 
-__all__ = ["Chain", "ChainBatch", "FinalEnergy", "OsmpsError", "LIB_PATH", "lib"]
+__all__ = ["Chain", "ChainBatch", "FinalEnergy", "PendingEntropy", "OsmpsError", "LIB_PATH", "lib"]
 
 _PREC = {"fp64": OSMPS_FP64, "mixed": OSMPS_MIXED}
 
@@ -62,8 +62,10 @@ class Chain:
     # ---- lifetime -------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None):
+            lib.osmps_ed_measure_wait(self._h)
             lib.osmps_ed_destroy(self._h)
             self._h = None
+            self._pending = []
 
     def __del__(self):
         try:
@@ -258,6 +260,56 @@ class Chain:
         lp = lam.ctypes.data_as(C.POINTER(C.c_double)) if spectrum else None
         check(lib.osmps_ed_schmidt_entropy(self._h, _dptr(psi), int(c), lp, C.byref(S)), "osmps_ed_schmidt_entropy")
         return (S.value, lam) if spectrum else S.value
+
+    def set_sm_count(self, nsm=0):
+        """Size the handle's grids for nsm SMs (0: all of the device)."""
+        check(lib.osmps_ed_set_sm_count(self._h, int(nsm)), "osmps_ed_set_sm_count")
+
+    def schmidt_entropy_async(self, psi, cut=-1, spectrum=False):
+        """Enqueues the bond entropy of psi without blocking; psi may be changed
+        right after.  Returns a PendingEntropy whose values are valid after
+        measure_wait()."""
+        self._check_state(psi)
+        c = self.L // 2 if cut in (-1, None) else int(cut)
+        n = 1 << min(c, self.L - c)
+        p = PendingEntropy(n if spectrum else 0)
+        lp = p._lam.ctypes.data_as(C.POINTER(C.c_double)) if spectrum else None
+        check(lib.osmps_ed_schmidt_entropy_async(self._h, _dptr(psi), int(c), p._S.ctypes.data_as(
+            C.POINTER(C.c_double)), lp), "osmps_ed_schmidt_entropy_async")
+        if not hasattr(self, "_pending"):
+            self._pending = []
+        self._pending.append(p)
+        return p
+
+    def measure_wait(self):
+        """Blocks until every pending asynchronous measurement has its values."""
+        st = lib.osmps_ed_measure_wait(self._h)
+        for p in getattr(self, "_pending", []):
+            p._done = st == 0
+        self._pending = []
+        check(st, "osmps_ed_measure_wait")
+
+
+class PendingEntropy:
+    """Result of Chain.schmidt_entropy_async: S (and the Schmidt spectrum,
+    descending, when asked for) once Chain.measure_wait() has returned."""
+
+    def __init__(self, n):
+        self._S = np.zeros(1)
+        self._lam = np.zeros(n)
+        self._done = False
+
+    @property
+    def S(self):
+        if not self._done:
+            raise RuntimeError("measurement pending: call Chain.measure_wait() first")
+        return float(self._S[0])
+
+    @property
+    def spectrum(self):
+        if not self._done:
+            raise RuntimeError("measurement pending: call Chain.measure_wait() first")
+        return self._lam
 
 
 class ChainBatch:

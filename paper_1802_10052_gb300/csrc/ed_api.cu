@@ -8,17 +8,60 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
-#include <new>
-#include <vector>
 #include <algorithm>
+#include <condition_variable>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
 
 #include "ed_internal.h"
 
 using namespace osmps;
 
+namespace {
+
+// Asynchronous bond entropy: the Gram product rho = psi_A psi_A^dag runs on the
+// caller's stream (psi may be overwritten as soon as it is enqueued); the
+// Hermitian eigen-solve and the entropy sum run on a lowest-priority
+// non-blocking side stream, driven by a worker thread of the handle because
+// the eigen-solver blocks its host thread.  Two rho buffers (slots) let the
+// caller run ahead by up to two measurements.
+struct AsyncJob {
+    int slot;
+    int n;
+    double *S_host;
+    double *lambda_host;
+};
+
+struct AsyncMeas {
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    bool busy[2] = {false, false};  // slot holds a job not yet finished
+    std::vector<AsyncJob> queue;
+    int next_slot = 0;
+    osmps_status err = OSMPS_OK;    // first failure of a job, returned by the wait
+    int64_t launches = 0;           // kernels launched on the side stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr};
+    void *rho[2] = {nullptr, nullptr};
+    size_t rho_bytes[2] = {0, 0};
+    double *lam[2] = {nullptr, nullptr};   // lambda (n) and S on the device
+    size_t lam_bytes[2] = {0, 0};
+    double *host[2] = {nullptr, nullptr};  // pinned staging of lambda and S
+    size_t host_bytes[2] = {0, 0};
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+}  // namespace
+
 struct osmps_ed {
     Handle h;
     bool reorth_set;
+    AsyncMeas *am;
 };
 
 namespace osmps {
@@ -305,6 +348,105 @@ void destroy_handle(Handle *h) {
     dev_free(h, h->lam_dev, 0);
 }
 
+void async_worker(Handle *h, AsyncMeas *am) {
+    cudaSetDevice(h->device);
+    std::unique_lock<std::mutex> lock(am->mu);
+    for (;;) {
+        am->cv.wait(lock, [am] { return am->stop || !am->queue.empty(); });
+        if (am->queue.empty()) return;  // stop requested and nothing left
+        const AsyncJob job = am->queue.front();
+        am->queue.erase(am->queue.begin());
+        const int sl = job.slot, n = job.n;
+        void *ws = am->ws;
+        size_t ws_bytes = am->ws_bytes;
+        int64_t launches = 0;
+        lock.unlock();
+        osmps_status st = from_cuda(cudaStreamWaitEvent(am->side, am->ready[sl], 0));
+        if (st == OSMPS_OK)
+            st = schmidt_eig_on(h, am->side, &ws, &ws_bytes, false, &launches, am->rho[sl], n, am->lam[sl],
+                                am->lam[sl] + n);
+        if (st == OSMPS_OK)
+            st = from_cuda(cudaMemcpyAsync(am->host[sl], am->lam[sl], sizeof(double) * (n + 1),
+                                           cudaMemcpyDeviceToHost, am->side));
+        if (st == OSMPS_OK) st = from_cuda(cudaStreamSynchronize(am->side));
+        if (st == OSMPS_OK) {
+            if (job.lambda_host) std::memcpy(job.lambda_host, am->host[sl], sizeof(double) * n);
+            if (job.S_host) *job.S_host = am->host[sl][n];
+        }
+        lock.lock();
+        am->ws = ws;
+        am->ws_bytes = ws_bytes;
+        am->launches += launches;
+        if (st != OSMPS_OK && am->err == OSMPS_OK) am->err = st;
+        am->busy[sl] = false;
+        am->cv.notify_all();
+    }
+}
+
+// Stops the worker after its queued jobs and frees the side resources.
+void destroy_async(AsyncMeas *am) {
+    if (am == nullptr) return;
+    {
+        std::lock_guard<std::mutex> lock(am->mu);
+        am->stop = true;
+    }
+    am->cv.notify_all();
+    if (am->worker.joinable()) am->worker.join();
+    if (am->side) cudaStreamSynchronize(am->side);
+    for (int i = 0; i < 2; ++i) {
+        if (am->ready[i]) cudaEventDestroy(am->ready[i]);
+        if (am->rho[i]) cudaFree(am->rho[i]);
+        if (am->lam[i]) cudaFree(am->lam[i]);
+        if (am->host[i]) cudaFreeHost(am->host[i]);
+    }
+    if (am->ws) cudaFree(am->ws);
+    if (am->side) cudaStreamDestroy(am->side);
+    delete am;
+}
+
+osmps_status create_async(Handle *h, AsyncMeas **out) {
+    AsyncMeas *am = new (std::nothrow) AsyncMeas();
+    if (am == nullptr) return OSMPS_ENOMEM;
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&am->side, cudaStreamNonBlocking, least);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&am->ready[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy_async(am);
+        return from_cuda(e);
+    }
+    try {
+        am->worker = std::thread(async_worker, h, am);
+    } catch (...) {
+        destroy_async(am);
+        return OSMPS_ENOMEM;
+    }
+    *out = am;
+    return OSMPS_OK;
+}
+
+// Device (or pinned host) buffer of at least `bytes`, not counted in the handle's bytes.
+osmps_status grow_untracked(void **p, size_t *cap, size_t bytes, bool pinned_host) {
+    if (bytes <= *cap) return OSMPS_OK;
+    if (*p) {
+        if (pinned_host)
+            cudaFreeHost(*p);
+        else
+            cudaFree(*p);
+    }
+    *p = nullptr;
+    *cap = 0;
+    const cudaError_t e = pinned_host ? cudaMallocHost(p, bytes) : cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return from_cuda(e);
+    }
+    *cap = bytes;
+    return OSMPS_OK;
+}
+
 }  // namespace
 
 namespace osmps {
@@ -462,6 +604,8 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
 
 osmps_status osmps_ed_destroy(osmps_ed_t *ed) {
     if (ed == nullptr) return OSMPS_OK;
+    destroy_async(ed->am);
+    ed->am = nullptr;
     destroy_handle(&ed->h);
     delete ed;
     return OSMPS_OK;
@@ -492,6 +636,15 @@ osmps_status osmps_ed_set_reorth(osmps_ed_t *ed, int mode) {
     if (ed == nullptr || (mode != 0 && mode != 1)) return OSMPS_EINVAL;
     ed->h.reorth = mode;
     ed->reorth_set = true;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    int dev_sm = 0;
+    CK(cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, ed->h.device));
+    if (nsm < 0 || nsm > dev_sm) return OSMPS_EINVAL;
+    ed->h.nsm = nsm == 0 ? dev_sm : nsm;
     return OSMPS_OK;
 }
 
@@ -747,6 +900,60 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
     CK(cudaStreamSynchronize(h->stream));
     if (S) *S = Sv;
     return OSMPS_OK;
+}
+
+osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int cut, double *S, double *lambda) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    CKS(check_state_ptr(h, psi));
+    const int L = h->L;
+    if (cut == -1) cut = L / 2;
+    if (L < 2 || cut < 1 || cut > L - 1) return OSMPS_EINVAL;
+    const int ls = cut < L - cut ? cut : L - cut;
+    const int n = 1 << ls;
+    if (ed->am == nullptr) CKS(create_async(h, &ed->am));
+    AsyncMeas *am = ed->am;
+    int sl;
+    {
+        // wait (host) until the next slot's previous job has finished
+        std::unique_lock<std::mutex> lock(am->mu);
+        sl = am->next_slot;
+        am->cv.wait(lock, [am, sl] { return !am->busy[sl]; });
+    }
+    CKS(grow_untracked(&am->rho[sl], &am->rho_bytes[sl], (size_t)n * n * h->esize, false));
+    CKS(grow_untracked((void **)&am->lam[sl], &am->lam_bytes[sl], sizeof(double) * (n + 1), false));
+    CKS(grow_untracked((void **)&am->host[sl], &am->host_bytes[sl], sizeof(double) * (n + 1), true));
+    int nn = 0;
+    {
+        const cudaError_t ge = launch_gram(h, psi, cut, am->rho[sl], &nn);
+        if (ge == cudaErrorNotSupported) {
+            cudaGetLastError();
+            return OSMPS_EUNSUPPORTED;
+        }
+        CK(ge);
+    }
+    CK(cudaEventRecord(am->ready[sl], h->stream));
+    {
+        std::lock_guard<std::mutex> lock(am->mu);
+        am->busy[sl] = true;
+        am->queue.push_back(AsyncJob{sl, nn, S, lambda});
+        am->next_slot = sl ^ 1;
+    }
+    am->cv.notify_all();
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_measure_wait(osmps_ed_t *ed) {
+    if (ed == nullptr) return OSMPS_EINVAL;
+    AsyncMeas *am = ed->am;
+    if (am == nullptr) return OSMPS_OK;
+    std::unique_lock<std::mutex> lock(am->mu);
+    am->cv.wait(lock, [am] { return !am->busy[0] && !am->busy[1]; });
+    ed->h.launches += am->launches;
+    am->launches = 0;
+    const osmps_status st = am->err;
+    am->err = OSMPS_OK;
+    return st;
 }
 
 // ---------------------------------------------------------------------------

@@ -116,6 +116,9 @@ cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_o
 bool gram_tc_supported(int n, long long K);
 cudaError_t gram_tc_launch(Handle *h, const void *psi, int n, long long K, void *rho, float *planes, float *G);
 osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev);
+// the same on a given stream and workspace (tracked: the workspace counts in the handle's owned bytes)
+osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void **ws, size_t *ws_bytes, bool tracked,
+                            int64_t *launches, void *rho, int n, double *lambda_dev, double *S_dev);
 
 // Device memory owned by a handle.
 struct Handle {

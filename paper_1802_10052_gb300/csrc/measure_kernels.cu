@@ -464,9 +464,16 @@ __global__ void entropy_kernel(const T *w, int n, double *lambda, double *S) {
     }
 }
 
-osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev) {
+// One cuSOLVER handle serves the process; its use (and its lazy loading) is
+// serialised, so that an asynchronous measurement on a worker thread and a
+// synchronous one never share it at the same time.
+static std::mutex g_solver_mu;
+
+osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void **ws_p, size_t *ws_bytes_p, bool tracked,
+                            int64_t *launches, void *rho, int n, double *lambda_dev, double *S_dev) {
+    std::lock_guard<std::mutex> lock(g_solver_mu);
     if (!load_solver()) return OSMPS_EUNSUPPORTED;
-    if (g_solver.set_stream(g_solver.handle, h->stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+    if (g_solver.set_stream(g_solver.handle, stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
     int lwork = 0;
     const bool dbl = (h->prec == OSMPS_FP64);
     cusolverStatus_t st;
@@ -479,16 +486,26 @@ osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double
                                 (const cuComplex *)rho, n, (const float *)nullptr, &lwork);
     if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
     const size_t need = (size_t)lwork * (dbl ? sizeof(cuDoubleComplex) : sizeof(cuComplex)) + wbytes + 64;
-    if (need > h->solver_ws_bytes) {
-        if (h->solver_ws) dev_free(h, h->solver_ws, h->solver_ws_bytes);
-        h->solver_ws = nullptr;
-        h->solver_ws_bytes = 0;
-        cudaError_t err;
-        h->solver_ws = dev_alloc(h, need, &err);
+    if (need > *ws_bytes_p) {
+        if (*ws_p) {
+            if (tracked)
+                dev_free(h, *ws_p, *ws_bytes_p);
+            else
+                cudaFree(*ws_p);
+        }
+        *ws_p = nullptr;
+        *ws_bytes_p = 0;
+        cudaError_t err = cudaSuccess;
+        if (tracked) {
+            *ws_p = dev_alloc(h, need, &err);
+        } else if ((err = cudaMalloc(ws_p, need)) != cudaSuccess) {
+            cudaGetLastError();
+            *ws_p = nullptr;
+        }
         if (err != cudaSuccess) return OSMPS_ENOMEM;
-        h->solver_ws_bytes = need;
+        *ws_bytes_p = need;
     }
-    char *ws = (char *)h->solver_ws;
+    char *ws = (char *)*ws_p;
     int *info = (int *)ws;
     void *wvals = ws + 16;
     void *work = ws + 16 + ((wbytes + 15) & ~(size_t)15);
@@ -500,11 +517,16 @@ osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double
                             n, (float *)wvals, (cuComplex *)work, lwork, info);
     if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
     if (dbl)
-        entropy_kernel<double><<<1, 1024, 0, h->stream>>>((const double *)wvals, n, lambda_dev, S_dev);
+        entropy_kernel<double><<<1, 1024, 0, stream>>>((const double *)wvals, n, lambda_dev, S_dev);
     else
-        entropy_kernel<float><<<1, 1024, 0, h->stream>>>((const float *)wvals, n, lambda_dev, S_dev);
-    h->launches += 1;
+        entropy_kernel<float><<<1, 1024, 0, stream>>>((const float *)wvals, n, lambda_dev, S_dev);
+    *launches += 1;
     return cudaGetLastError() == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
+}
+
+osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev) {
+    return schmidt_eig_on(h, h->stream, &h->solver_ws, &h->solver_ws_bytes, true, &h->launches, rho, n, lambda_dev,
+                          S_dev);
 }
 
 }  // namespace osmps
