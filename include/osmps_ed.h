@@ -285,6 +285,22 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
 osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int cut, double *S,
                                             double *lambda);
 
+/*
+ * Eigen-solver of osmps_ed_schmidt_entropy_async.  ctas = 0: the library
+ * routine (cuSOLVER heevd) on the handle's worker thread.  ctas > 0: this
+ * library's kernels, enqueued by the calling thread on one lowest-priority
+ * stream per result slot: blocked Householder reduction of rho to real
+ * tridiagonal form (panels of 32 columns, one cooperative launch of at least
+ * `ctas` CTAs per panel, more when the CTAs' row slices would not fit in
+ * shared memory) with a trailing rank-64 update per panel, then every
+ * eigenvalue by Sturm-count multisection in the working precision, so that
+ * two measurements can run beside the caller's work on a few SMs each.
+ * Waits for outstanding measurements first.  EUNSUPPORTED (at the entropy
+ * call) when no CTA count up to the device's SMs fits.  Not from the paper
+ * (eigen-solver and scheduling).
+ */
+osmps_status osmps_ed_set_async_eigensolver(osmps_ed_t *ed, int ctas);
+
 /* Blocks until every osmps_ed_schmidt_entropy_async of this handle has
  * written its results; returns the first error among them (then clears it).
  * Call it before osmps_ed_destroy when measurements are outstanding. */

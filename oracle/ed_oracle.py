@@ -535,6 +535,19 @@ def schmidt_spectrum(psi: np.ndarray, L: int, cut: int | None = None) -> np.ndar
     return np.sort(np.linalg.eigvalsh(rho))[::-1]
 
 
+def schmidt_spectrum_small(psi: np.ndarray, L: int, cut: int | None = None) -> np.ndarray:
+    """The 2^min(l, L-l) Schmidt values of the cut after site l, descending.
+
+    Sec. IV, bond entropy: rho_A = M M^dagger and rho_B = (M^dagger M)^T have the
+    same nonzero spectrum (the squared singular values of M), so the smaller of
+    the two Gram matrices is diagonalised.
+    """
+    l = L // 2 if cut is None or cut < 0 else cut
+    M = psi.reshape(1 << l, 1 << (L - l))
+    G = M @ M.conj().T if l <= L - l else M.conj().T @ M
+    return np.sort(np.linalg.eigvalsh(G))[::-1]
+
+
 def entropy_from_spectrum(lam: np.ndarray) -> float:
     """S = -sum_j Lambda_j ln Lambda_j (natural log); Lambda <= 0 counts as 0."""
     lam = np.asarray(lam, dtype=np.float64)

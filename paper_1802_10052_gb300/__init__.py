@@ -265,6 +265,11 @@ class Chain:
         """Size the handle's grids for nsm SMs (0: all of the device)."""
         check(lib.osmps_ed_set_sm_count(self._h, int(nsm)), "osmps_ed_set_sm_count")
 
+    def set_async_eigensolver(self, ctas=0):
+        """Eigen-solver of schmidt_entropy_async: 0 = library routine on a worker
+        thread, > 0 = this library's reduction on (at least) that many CTAs."""
+        check(lib.osmps_ed_set_async_eigensolver(self._h, int(ctas)), "osmps_ed_set_async_eigensolver")
+
     def schmidt_entropy_async(self, psi, cut=-1, spectrum=False):
         """Enqueues the bond entropy of psi without blocking; psi may be changed
         right after.  Returns a PendingEntropy whose values are valid after

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libosmps_ed.so")
-SOURCES = ["ed_api.cu", "hpsi_kernels.cu", "vec_kernels.cu", "measure_kernels.cu", "gram_tc.cu", "batch_kernels.cu",
+SOURCES = ["ed_api.cu", "hpsi_kernels.cu", "vec_kernels.cu", "measure_kernels.cu", "gram_tc.cu", "eig_kernels.cu", "batch_kernels.cu",
            "batch_api.cu", "gate_kernels.cu", "rdm_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

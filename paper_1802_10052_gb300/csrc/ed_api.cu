@@ -54,6 +54,16 @@ struct AsyncMeas {
     size_t host_bytes[2] = {0, 0};
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // own eigen-solver (osmps_ed_set_async_eigensolver > 0): every step of a
+    // measurement is enqueued by the calling thread on the slot's stream
+    int own_G = 0;                           // CTAs of the cooperative reduction; 0 = library solver
+    cudaStream_t ss[2] = {nullptr, nullptr};  // per-slot streams (lowest priority, non-blocking)
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    void *tws[2] = {nullptr, nullptr};
+    size_t tws_bytes[2] = {0, 0};
+    int *err_dev = nullptr;                  // 2 ints: bounded waits of the reduction gave up
+    int *err_host = nullptr;                 // pinned copies
+    AsyncJob job[2] = {};                    // the job a slot holds in this mode
 };
 
 }  // namespace
@@ -401,7 +411,53 @@ void destroy_async(AsyncMeas *am) {
     }
     if (am->ws) cudaFree(am->ws);
     if (am->side) cudaStreamDestroy(am->side);
+    for (int i = 0; i < 2; ++i) {
+        if (am->ss[i]) cudaStreamSynchronize(am->ss[i]);
+        if (am->done[i]) cudaEventDestroy(am->done[i]);
+        if (am->tws[i]) cudaFree(am->tws[i]);
+        if (am->ss[i]) cudaStreamDestroy(am->ss[i]);
+    }
+    if (am->err_dev) cudaFree(am->err_dev);
+    if (am->err_host) cudaFreeHost(am->err_host);
     delete am;
+}
+
+// Streams, events and error words of the own-solver mode (created once).
+osmps_status ensure_own_mode(AsyncMeas *am) {
+    if (am->err_dev != nullptr) return OSMPS_OK;
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithPriority(&am->ss[i], cudaStreamNonBlocking, least);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&am->done[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&am->err_host, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&am->err_dev, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(am->err_dev, 0, 2 * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (am->err_dev) cudaFree(am->err_dev);
+        am->err_dev = nullptr;
+        return from_cuda(e);
+    }
+    am->err_host[0] = am->err_host[1] = 0;
+    return OSMPS_OK;
+}
+
+// Own-solver mode: waits for slot sl's measurement and writes its results.
+osmps_status finish_own_slot(AsyncMeas *am, int sl) {
+    if (!am->busy[sl]) return OSMPS_OK;
+    osmps_status st = from_cuda(cudaEventSynchronize(am->done[sl]));
+    if (st == OSMPS_OK && am->err_host[sl] != 0) st = OSMPS_ETIMEOUT;
+    if (st == OSMPS_OK) {
+        const AsyncJob &j = am->job[sl];
+        if (j.lambda_host) std::memcpy(j.lambda_host, am->host[sl], sizeof(double) * j.n);
+        if (j.S_host) *j.S_host = am->host[sl][j.n];
+    }
+    std::lock_guard<std::mutex> lock(am->mu);
+    am->busy[sl] = false;
+    if (st != OSMPS_OK && am->err == OSMPS_OK) am->err = st;
+    return st;
 }
 
 osmps_status create_async(Handle *h, AsyncMeas **out) {
@@ -444,6 +500,53 @@ osmps_status grow_untracked(void **p, size_t *cap, size_t bytes, bool pinned_hos
         return from_cuda(e);
     }
     *cap = bytes;
+    return OSMPS_OK;
+}
+
+osmps_status entropy_async_own(Handle *h, AsyncMeas *am, const void *psi, int cut, int n, double *S,
+                               double *lambda) {
+    const int sl = am->next_slot;
+    CKS(finish_own_slot(am, sl));  // the slot's previous measurement (host wait)
+    const int G = trd_ctas(n, h->prec, am->own_G, h->device);
+    if (G == 0) return OSMPS_EUNSUPPORTED;
+    CKS(grow_untracked(&am->rho[sl], &am->rho_bytes[sl], (size_t)n * n * h->esize, false));
+    CKS(grow_untracked((void **)&am->lam[sl], &am->lam_bytes[sl], sizeof(double) * (n + 1), false));
+    CKS(grow_untracked((void **)&am->host[sl], &am->host_bytes[sl], sizeof(double) * (n + 1), true));
+    CKS(grow_untracked(&am->tws[sl], &am->tws_bytes[sl], trd_workspace_bytes(n, h->prec, G), false));
+    int nn = 0;
+    {
+        const cudaError_t ge = launch_gram(h, psi, cut, am->rho[sl], &nn);
+        if (ge == cudaErrorNotSupported) {
+            cudaGetLastError();
+            return OSMPS_EUNSUPPORTED;
+        }
+        CK(ge);
+    }
+    cudaStream_t st = am->ss[sl];
+    CK(cudaEventRecord(am->ready[sl], h->stream));
+    CK(cudaStreamWaitEvent(st, am->ready[sl], 0));
+    CK(cudaMemsetAsync(am->err_dev + sl, 0, sizeof(int), st));
+    TrdRun run{h->prec, h->device, st, G, am->tws[sl], am->tws_bytes[sl], am->err_dev + sl, &h->launches};
+    double *w = nullptr;
+    {
+        const cudaError_t te = trd_eigvals(run, am->rho[sl], nn, &w);
+        if (te == cudaErrorNotSupported) {
+            cudaGetLastError();
+            return OSMPS_EUNSUPPORTED;
+        }
+        CK(te);
+    }
+    CK(launch_entropy(st, w, nn, am->lam[sl], am->lam[sl] + nn));
+    h->launches += 1;
+    CK(cudaMemcpyAsync(am->host[sl], am->lam[sl], sizeof(double) * (nn + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(am->err_host + sl, am->err_dev + sl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(am->done[sl], st));
+    {
+        std::lock_guard<std::mutex> lock(am->mu);
+        am->busy[sl] = true;
+        am->job[sl] = AsyncJob{sl, nn, S, lambda};
+        am->next_slot = sl ^ 1;
+    }
     return OSMPS_OK;
 }
 
@@ -913,6 +1016,7 @@ osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int
     const int n = 1 << ls;
     if (ed->am == nullptr) CKS(create_async(h, &ed->am));
     AsyncMeas *am = ed->am;
+    if (am->own_G > 0) return entropy_async_own(h, am, psi, cut, n, S, lambda);
     int sl;
     {
         // wait (host) until the next slot's previous job has finished
@@ -943,10 +1047,25 @@ osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int
     return OSMPS_OK;
 }
 
+osmps_status osmps_ed_set_async_eigensolver(osmps_ed_t *ed, int ctas) {
+    if (ed == nullptr || ctas < 0) return OSMPS_EINVAL;
+    if (ed->am == nullptr) CKS(create_async(&ed->h, &ed->am));
+    CKS(osmps_ed_measure_wait(ed));  // no outstanding measurement changes mode
+    if (ctas > 0) CKS(ensure_own_mode(ed->am));
+    ed->am->own_G = ctas;
+    return OSMPS_OK;
+}
+
 osmps_status osmps_ed_measure_wait(osmps_ed_t *ed) {
     if (ed == nullptr) return OSMPS_EINVAL;
     AsyncMeas *am = ed->am;
     if (am == nullptr) return OSMPS_OK;
+    if (am->own_G > 0) {
+        // oldest slot first (results land in the order the calls were made)
+        const int first = am->next_slot;
+        finish_own_slot(am, first);
+        finish_own_slot(am, first ^ 1);
+    }
     std::unique_lock<std::mutex> lock(am->mu);
     am->cv.wait(lock, [am] { return !am->busy[0] && !am->busy[1]; });
     ed->h.launches += am->launches;

@@ -116,6 +116,27 @@ cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_o
 bool gram_tc_supported(int n, long long K);
 cudaError_t gram_tc_launch(Handle *h, const void *psi, int n, long long K, void *rho, float *planes, float *G);
 osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev);
+// S and the descending spectrum from ascending FP64 eigenvalues w (n values) on a stream
+cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *lambda_dev, double *S_dev);
+
+// eig_kernels.cu: eigenvalues of the Hermitian rho (the Gram product's row-major
+// upper triangle read as a column-major lower triangle; overwritten) by blocked
+// Householder tridiagonalization on G cooperative CTAs and Sturm multisection.
+struct TrdRun {
+    int prec;
+    int device;
+    cudaStream_t stream;
+    int G;                      // CTAs of the cooperative panel kernel (all resident)
+    void *ws;                   // workspace of trd_workspace_bytes(n, prec, G) bytes
+    size_t ws_bytes;
+    int *error;                 // device int set to 1 when a bounded wait gave up
+    int64_t *launches;          // incremented by the kernels launched (may be null)
+};
+int trd_ctas(int n, int prec, int want, int device);
+size_t trd_workspace_bytes(int n, int prec, int G);
+// ascending FP64 eigenvalues in the workspace (*w points to them)
+cudaError_t trd_eigvals(const TrdRun &run, void *rho, int n, double **w);
+
 // the same on a given stream and workspace (tracked: the workspace counts in the handle's owned bytes)
 osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void **ws, size_t *ws_bytes, bool tracked,
                             int64_t *launches, void *rho, int n, double *lambda_dev, double *S_dev);

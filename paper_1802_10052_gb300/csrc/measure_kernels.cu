@@ -298,20 +298,25 @@ namespace osmps {
 // ---------------------------------------------------------------------------
 constexpr int kGT = 64, kGK = 16;
 
+// Split K (blockIdx.z = split): split z sums k in [z*kchunk, min(K, (z+1)*kchunk))
+// into its own n x n slice of rho (slices summed afterwards in a fixed order).
 template <typename T>
 __global__ void __launch_bounds__(256) gram_kernel(const typename ZV<T>::c *psi, int n, long long K, long long sx,
-                                                   long long sk, typename ZV<T>::c *rho) {
+                                                   long long sk, long long kchunk, typename ZV<T>::c *rho) {
     typedef typename ZV<T>::c C;
     __shared__ C As[kGK][kGT + 1];
     __shared__ C Bs[kGK][kGT + 1];
     const int x0 = blockIdx.y * kGT, y0 = blockIdx.x * kGT;
+    const long long kbeg = (long long)blockIdx.z * kchunk;
+    const long long kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+    rho += (size_t)blockIdx.z * n * n;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     T accr[4][4], acci[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = (T)0;
-    for (long long k0 = 0; k0 < K; k0 += kGK) {
+    for (long long k0 = kbeg; k0 < kend; k0 += kGK) {
         // load 64 x 16 slices of rows x0.. and y0..
         for (int idx = threadIdx.x; idx < kGT * kGK; idx += 256) {
             int r, kk;
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const typename ZV<T>::c *psi,
             }
             const long long k = k0 + kk;
             C a = C{(T)0, (T)0}, b = C{(T)0, (T)0};
-            if (k < K) {
+            if (k < kend) {
                 if (x0 + r < n) a = psi[(long long)(x0 + r) * sx + k * sk];
                 if (y0 + r < n) b = psi[(long long)(y0 + r) * sx + k * sk];
             }
@@ -357,6 +362,20 @@ __global__ void __launch_bounds__(256) gram_kernel(const typename ZV<T>::c *psi,
             const int x = x0 + ty + 16 * i, y = y0 + tx + 16 * j;
             if (x < n && y < n) rho[(size_t)x * n + y] = C{accr[i][j], acci[i][j]};
         }
+}
+
+// rho = sum over the nsplit slices of part (fixed order, FP64 accumulation)
+template <typename T>
+__global__ void gram_split_sum_kernel(const typename ZV<T>::c *part, int nsplit, size_t nn, typename ZV<T>::c *rho) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int z = 0; z < nsplit; ++z) {
+            const typename ZV<T>::c v = part[(size_t)z * nn + i];
+            re += (double)v.x;
+            im += (double)v.y;
+        }
+        rho[i] = typename ZV<T>::c{(T)re, (T)im};
+    }
 }
 
 cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_out) {
@@ -394,12 +413,44 @@ cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_o
         float *G = planes + (size_t)n * 4 * (size_t)K;
         return gram_tc_launch(h, psi, n, K, rho, planes, G);
     }
-    dim3 grid((n + kGT - 1) / kGT, (n + kGT - 1) / kGT);
+    // few output tiles (small n, long K): split K so that the grid fills the GPU
+    const long long tiles = (long long)((n + kGT - 1) / kGT) * ((n + kGT - 1) / kGT);
+    long long nsplit = (4ll * h->nsm + tiles - 1) / tiles;
+    if (nsplit > K / 1024) nsplit = K / 1024;
+    if (nsplit < 1) nsplit = 1;
+    const long long kchunk = ((K + nsplit - 1) / nsplit + kGK - 1) / kGK * kGK;
+    nsplit = (K + kchunk - 1) / kchunk;
+    void *out = rho;
+    const size_t nn = (size_t)n * n;
+    if (nsplit > 1) {
+        const size_t need = (size_t)nsplit * nn * h->esize;
+        if (need > h->gram_aux_bytes) {
+            dev_free(h, h->gram_aux, h->gram_aux_bytes);
+            h->gram_aux = nullptr;
+            h->gram_aux_bytes = 0;
+            cudaError_t err;
+            h->gram_aux = dev_alloc(h, need, &err);
+            if (err != cudaSuccess) return err;
+            h->gram_aux_bytes = need;
+        }
+        out = h->gram_aux;
+    }
+    dim3 grid((n + kGT - 1) / kGT, (n + kGT - 1) / kGT, (unsigned)nsplit);
     if (h->prec == OSMPS_FP64)
-        gram_kernel<double><<<grid, 256, 0, h->stream>>>((const double2 *)psi, n, K, sx, sk, (double2 *)rho);
+        gram_kernel<double><<<grid, 256, 0, h->stream>>>((const double2 *)psi, n, K, sx, sk, kchunk, (double2 *)out);
     else
-        gram_kernel<float><<<grid, 256, 0, h->stream>>>((const float2 *)psi, n, K, sx, sk, (float2 *)rho);
+        gram_kernel<float><<<grid, 256, 0, h->stream>>>((const float2 *)psi, n, K, sx, sk, kchunk, (float2 *)out);
     h->launches += 1;
+    if (nsplit > 1) {
+        const unsigned g = (unsigned)((nn + 255) / 256 < 4096 ? (nn + 255) / 256 : 4096);
+        if (h->prec == OSMPS_FP64)
+            gram_split_sum_kernel<double><<<g, 256, 0, h->stream>>>((const double2 *)out, (int)nsplit, nn,
+                                                                     (double2 *)rho);
+        else
+            gram_split_sum_kernel<float><<<g, 256, 0, h->stream>>>((const float2 *)out, (int)nsplit, nn,
+                                                                    (float2 *)rho);
+        h->launches += 1;
+    }
     return cudaGetLastError();
 }
 
@@ -522,6 +573,11 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void **ws_p, size_t 
         entropy_kernel<float><<<1, 1024, 0, stream>>>((const float *)wvals, n, lambda_dev, S_dev);
     *launches += 1;
     return cudaGetLastError() == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
+}
+
+cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *lambda_dev, double *S_dev) {
+    entropy_kernel<double><<<1, 1024, 0, stream>>>(w, n, lambda_dev, S_dev);
+    return cudaGetLastError();
 }
 
 osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev) {

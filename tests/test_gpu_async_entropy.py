@@ -97,3 +97,108 @@ def test_async_argument_errors():
         c.schmidt_entropy_async(x, cut=8)
     c.measure_wait()          # nothing outstanding
     c.close()
+
+
+# ---- this library's eigen-solver on a few CTAs (osmps_ed_set_async_eigensolver) ----
+
+def own_entropy(c, x, cut=-1, ctas=16):
+    c.set_async_eigensolver(ctas)
+    p = c.schmidt_entropy_async(x, cut=cut, spectrum=True)
+    c.measure_wait()
+    return p.S, p.spectrum
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("L,cut", [(2, 1), (3, -1), (3, 2), (8, -1), (9, 2), (9, 7), (12, -1), (13, -1), (13, 9)])
+def test_own_solver_matches_oracle(L, cut, prec):
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
+    x = to_dev(si.gaussian_state(L, 60 + L), prec)
+    ref = x.cpu().numpy().astype(np.complex128)
+    l = L // 2 if cut == -1 else cut
+    want = O.schmidt_spectrum_small(ref, L, l)
+    S, lam = own_entropy(c, x, cut)
+    n = 1 << min(l, L - l)
+    np.testing.assert_allclose(lam, want[:n], atol=1e-13 if prec == "fp64" else 1e-6)
+    assert abs(S - O.entropy_from_spectrum(want)) < (1e-12 if prec == "fp64" else 1e-5)
+    c.close()
+
+
+@pytest.mark.parametrize("L,cut,ctas", [(14, -1, 8), (16, -1, 16), (19, -1, 24), (18, 8, 152)])
+def test_own_solver_tensor_core_gram_matches_oracle(L, cut, ctas):
+    x = to_dev(si.gaussian_state(L, 80 + L), "mixed")
+    ref = x.cpu().numpy().astype(np.complex128)
+    l = L // 2 if cut == -1 else cut
+    want = O.schmidt_spectrum_small(ref, L, l)
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec="mixed")
+    S, lam = own_entropy(c, x, cut, ctas)
+    n = 1 << min(l, L - l)
+    np.testing.assert_allclose(lam, want[:n], atol=2e-6)
+    assert abs(S - O.entropy_from_spectrum(want)) < 1e-5
+    c.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_own_solver_page_value_and_special_states(prec):
+    import math
+    L = 20
+    m = n = 1 << (L // 2)
+    page = sum(1.0 / k for k in range(n + 1, m * n + 1)) - (m - 1) / (2.0 * n)
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
+    x = to_dev(si.gaussian_state(L, 7), prec)
+    S, lam = own_entropy(c, x)
+    assert abs(S - page) < 2e-3
+    assert abs(lam.sum() - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
+    c.init_basis_state(x, si.neel_index(L))
+    S, lam = own_entropy(c, x)
+    assert abs(S) < 1e-6 and abs(lam[0] - 1.0) < 1e-6
+    g = to_dev(si.ghz_state(L), prec)
+    S, lam = own_entropy(c, g)
+    assert abs(S - math.log(2.0)) < (1e-12 if prec == "fp64" else 1e-6)
+    np.testing.assert_allclose(lam[:2], 0.5, atol=1e-7)
+    np.testing.assert_allclose(lam[2:], 0.0, atol=1e-7)
+    c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+def test_own_solver_pipeline_against_library(prec, tol):
+    """Three overlapped measurements along an evolution on the own solver (two
+    slots, the third call waits for the first), each against the library
+    solver's synchronous entropy of the same stored state."""
+    L = 16
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+    c.set_async_eigensolver(16)
+    x = c.new_state()
+    c.init_basis_state(x, 0)
+    snaps, pend = [], []
+    for _ in range(3):
+        c.krylov_evolve(x, 0.1, 2, 16)
+        snaps.append(x.clone())
+        pend.append(c.schmidt_entropy_async(x, spectrum=True))
+    c.measure_wait()
+    for s, p in zip(snaps, pend):
+        S, lam = c.schmidt_entropy(s, spectrum=True)
+        assert abs(p.S - S) < tol
+        np.testing.assert_allclose(p.spectrum, lam, atol=tol)
+    c.set_async_eigensolver(0)
+    p = c.schmidt_entropy_async(snaps[-1])
+    c.measure_wait()
+    assert abs(p.S - pend[-1].S) < tol
+    c.close()
+
+
+def test_own_solver_full_size_quench():
+    """L = 24 complex64 quench state (n = 4096): own solver on 16 CTAs against the
+    library solver: the Schmidt values above 1e-4 to 2e-6, S to the FP32 noise
+    floor of the tiny eigenvalues."""
+    L = 24
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    x = c.new_state()
+    c.init_basis_state(x, 0)
+    c.krylov_evolve(x, 0.1, 5, 20)
+    S_lib, lam_lib = c.schmidt_entropy(x, spectrum=True)
+    S, lam = own_entropy(c, x, -1, 16)
+    big = lam_lib > 1e-4
+    np.testing.assert_allclose(lam[big], lam_lib[big], atol=2e-6)
+    assert abs(lam.sum() - 1.0) < 1e-4
+    assert abs(S - S_lib) < 5e-3
+    c.close()

@@ -69,14 +69,16 @@ def test_special_states(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("L,cut", [(2, 1), (3, -1), (3, 2), (8, -1), (9, -1), (9, 2), (9, 7), (12, -1), (13, -1), (13, 9)])
+@pytest.mark.parametrize("L,cut", [(2, 1), (3, -1), (3, 2), (8, -1), (9, -1), (9, 2), (9, 7), (12, -1), (13, -1), (13, 9),
+                                   (16, 3), (16, 13), (18, 1), (18, 6), (17, 11)])
 def test_schmidt_spectrum_matches_oracle(L, cut, prec):
+    """Includes small blocks with long contractions (split over K on the CUDA cores)."""
     c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
     psi = si.gaussian_state(L, 60 + L)
     x = to_dev(psi, prec)
     ref_state = x.cpu().numpy().astype(np.complex128)
     l = L // 2 if cut == -1 else cut
-    want = O.schmidt_spectrum(ref_state, L, l)
+    want = O.schmidt_spectrum_small(ref_state, L, l)
     S, lam = c.schmidt_entropy(x, cut=cut, spectrum=True)
     n = 1 << min(l, L - l)
     tol = 1e-13 if prec == "fp64" else 1e-6
@@ -106,7 +108,7 @@ def test_tensor_core_gram_matches_oracle(L, cut):
     x = to_dev(psi, "mixed")
     ref_state = x.cpu().numpy().astype(np.complex128)
     l = L // 2 if cut == -1 else cut
-    want = O.schmidt_spectrum(ref_state, L, l)
+    want = O.schmidt_spectrum_small(ref_state, L, l)
     c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec="mixed")
     c.set_gram_mode(2)
     S_tc, lam_tc = c.schmidt_entropy(x, cut=cut, spectrum=True)

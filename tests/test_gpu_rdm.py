@@ -57,12 +57,12 @@ def test_pair_rdms_full_size_sampled():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_entropy_sweep_matches_oracle(prec):
-    L = 12
+@pytest.mark.parametrize("L", [12, 17])
+def test_entropy_sweep_matches_oracle(prec, L):
     psi = si.gaussian_state(L, 95)
     c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec=prec)
     x = to_dev(psi, prec)
     ref = x.cpu().numpy().astype(np.complex128)
     S = c.entropy_sweep(x)
-    want = [O.schmidt_entropy(ref, L, l) for l in range(1, L)]
+    want = [O.entropy_from_spectrum(O.schmidt_spectrum_small(ref, L, l)) for l in range(1, L)]
     np.testing.assert_allclose(S, want, atol=1e-12 if prec == "fp64" else 1e-5)

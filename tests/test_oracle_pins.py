@@ -279,6 +279,19 @@ def test_schmidt_spectrum_invariants_and_svd():
         np.testing.assert_allclose(lam, right, atol=1e-13)
 
 
+def test_schmidt_spectrum_small_side_equals_singular_values():
+    """Both branches (left block smaller / larger) against the squared singular
+    values of M, which a plain SVD fixes independently of either Gram matrix."""
+    L = 9
+    psi = si.gaussian_state(L, 44)
+    for l in (1, 3, 4, 5, 8):
+        M = psi.reshape(1 << l, 1 << (L - l))
+        sv = np.sort(np.linalg.svd(M, compute_uv=False) ** 2)[::-1]
+        lam = O.schmidt_spectrum_small(psi, L, l)
+        assert len(lam) == 1 << min(l, L - l)
+        np.testing.assert_allclose(lam, sv, atol=1e-13)
+
+
 def test_page_value():
     # Haar-random state, equal bipartition m = n: Page (1993) mean entropy.
     L = 14
