@@ -46,11 +46,11 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-trotter", action="store_true")
     ap.add_argument("--no-rdm", action="store_true")
-    ap.add_argument("--entropy", choices=["async", "sync"], default="async",
+    ap.add_argument("--entropy", choices=["async", "sync"], default="sync",
                     help="bond entropy per step: overlapped eigen-solve (async) or blocking (sync)")
     ap.add_argument("--main-priority", choices=["high", "default"], default="high",
                     help="priority of the stream the evolution runs on")
-    ap.add_argument("--profile-case", choices=["batch_L16"], default=None,
+    ap.add_argument("--profile-case", choices=["batch_L16", "gates_L24", "rdm_L24"], default=None,
                     help="run one small profiling workload and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -601,6 +601,28 @@ def profile_case(name):
             psi.copy_(start)
             b.lanczos_ground(psi, 1e-10)
         print(json.dumps({"profile_case": name, "iters_mean": float(b.iters.float().mean())}))
+    elif name == "gates_L24":
+        # NN chain L = 24 (J = h = 1), complex64, all-up start: two second-order Trotter steps
+        from paper_1802_10052_gb300 import Chain
+        L = 24
+        c = Chain(L, couplings=[1.0] + [0.0] * (L - 2), h=1.0, prec="mixed")
+        x = c.new_state()
+        c.init_basis_state(x, 0)
+        c.trotter_evolve(x, 0.01, 2, 2)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "norm": float(torch.linalg.vector_norm(x).item())}))
+        c.close()
+    elif name == "rdm_L24":
+        # L = 24 complex64 seeded Gaussian state: all 276 pair RDMs, twice
+        from paper_1802_10052_gb300 import Chain
+        L = 24
+        c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+        x = torch.from_numpy(si.gaussian_state(L, 24).astype(np.complex64)).cuda()
+        r2, _ = c.rdm_pairs(x)
+        r2, _ = c.rdm_pairs(x)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "trace_01": float(np.trace(r2[0]).real)}))
+        c.close()
     return 0
 
 

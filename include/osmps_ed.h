@@ -121,6 +121,12 @@ osmps_status osmps_ed_set_gram_mode(osmps_ed_t *ed, int mode);
  * (scheduling). */
 osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm);
 
+/* L2 prefetch distance of the H.psi passes: each CTA asks L2 (TMA prefetch)
+ * for the tiles it will stage `tiles` steps after the ones its shared-memory
+ * stages hold; 0 = off.  Default 1 for OSMPS_MIXED, 0 for OSMPS_FP64.
+ * 0 <= tiles <= 4.  Not from the paper (memory scheduling). */
+osmps_status osmps_ed_set_prefetch(osmps_ed_t *ed, int tiles);
+
 /* D = 2^L. */
 osmps_status osmps_ed_dim(const osmps_ed_t *ed, uint64_t *D);
 

@@ -265,6 +265,10 @@ class Chain:
         """Size the handle's grids for nsm SMs (0: all of the device)."""
         check(lib.osmps_ed_set_sm_count(self._h, int(nsm)), "osmps_ed_set_sm_count")
 
+    def set_prefetch(self, tiles):
+        """L2 prefetch distance of the H.psi passes (tiles ahead; 0 = off)."""
+        check(lib.osmps_ed_set_prefetch(self._h, int(tiles)), "osmps_ed_set_prefetch")
+
     def set_async_eigensolver(self, ctas=0):
         """Eigen-solver of schmidt_entropy_async: 0 = library routine on a worker
         thread, > 0 = this library's reduction on (at least) that many CTAs."""

@@ -655,6 +655,7 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
     for (int r = 0; r <= kMaxL; ++r) hd->Jr[r] = Jr[r];
     for (int b = 0; b < L; ++b) hd->hbit[b] = h;
     hd->reorth = 0;
+    hd->prefetch = (prec == OSMPS_FP64) ? 0 : 1;  // FP64 passes are bound by the FP64 pipe, not by latency
     cudaError_t err = cudaGetDevice(&hd->device);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&hd->nsm, cudaDevAttrMultiProcessorCount, hd->device);
     if (err != cudaSuccess) {
@@ -748,6 +749,12 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm) {
     CK(cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, ed->h.device));
     if (nsm < 0 || nsm > dev_sm) return OSMPS_EINVAL;
     ed->h.nsm = nsm == 0 ? dev_sm : nsm;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_prefetch(osmps_ed_t *ed, int tiles) {
+    if (ed == nullptr || tiles < 0 || tiles > 4) return OSMPS_EINVAL;
+    ed->h.prefetch = tiles;
     return OSMPS_OK;
 }
 

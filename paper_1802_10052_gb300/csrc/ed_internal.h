@@ -179,6 +179,7 @@ struct Handle {
     void *gram_aux;             // tensor-core Gram: TF32 hi/lo planes and G
     size_t gram_aux_bytes;
     int gram_mode;              // 0 automatic, 1 CUDA cores, 2 tensor cores
+    int prefetch;               // L2 prefetch distance of the H.psi passes (tiles)
     void *solver_ws;            // cuSOLVER workspace
     size_t solver_ws_bytes;
     double *lam_dev;

@@ -58,6 +58,7 @@ struct PassParams {
     long long ntiles;
     int stop_index;
     int L, c, o, g, ta, first, last, epilogue, rank;
+    int pf;                             // L2 prefetch distance in tiles beyond the shared-memory stages
     unsigned tile_bytes;
     T hb[kMaxL + 1];
 };
@@ -260,6 +261,36 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 if (lane == 0) atomicExch(p.err, 1);
                 failed = true;
                 break;
+            }
+        }
+        if (warp == 0 && lane == 0 && p.pf > 0) {
+            // warm L2 up to pf tiles beyond what the shared-memory stages hold:
+            // u of the pf-th tile after the ring, the stream pf tiles ahead
+            // (the nearer ones were requested by the previous iterations)
+            int crd[5];
+            const long long tp = t + (long long)(kStages - 1 + p.pf) * gridDim.x;
+            if (tp < p.ntiles) {
+                coords(tp, crd);
+                tma_prefetch_l2(&tm_u, p.rank, crd);
+            }
+            const long long tq = t + (long long)p.pf * gridDim.x;
+            if (has_stream && tq < p.ntiles) {
+                coords(tq, crd);
+                tma_prefetch_l2(&tm_s, p.rank, crd);
+            }
+            if (n == 0) {  // the first iteration also requests the nearer tiles
+                for (int k = 1; k < p.pf; ++k) {
+                    const long long tu = t + (long long)(kStages - 1 + k) * gridDim.x;
+                    if (tu < p.ntiles) {
+                        coords(tu, crd);
+                        tma_prefetch_l2(&tm_u, p.rank, crd);
+                    }
+                    const long long ts = t + (long long)k * gridDim.x;
+                    if (has_stream && ts < p.ntiles) {
+                        coords(ts, crd);
+                        tma_prefetch_l2(&tm_s, p.rank, crd);
+                    }
+                }
             }
         }
         const V *Ucur = U + (size_t)s * kTileV;
@@ -741,6 +772,7 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.last = last ? 1 : 0;
         p.epilogue = a.epilogue;
         p.rank = rank;
+        p.pf = h->prefetch;
         p.tile_bytes = (unsigned)((1u << (d.c + d.g)) * h->esize);
         for (int k = 0; k <= kMaxL; ++k) p.hb[k] = (T)h->hbit[k];
         const int grid = grid_for<T>(h, d.ntiles);

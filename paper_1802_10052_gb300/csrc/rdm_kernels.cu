@@ -19,6 +19,7 @@ namespace rdm {
 constexpr int kRdmThreads = 256;
 constexpr int kRdmBlocks = 48;  // blocks per pair
 constexpr int kRdmVals = 16;    // 4 diagonal + 6 (re, im) upper entries
+constexpr int kRdmBatch = 8;    // amplitude quadruples loaded together per thread
 
 template <typename T> struct Cr;
 template <> struct Cr<float> { typedef float2 C; };
@@ -47,30 +48,42 @@ __global__ void __launch_bounds__(kRdmThreads) pair_rdm_kernel(const typename Cr
 #pragma unroll
     for (int q = 0; q < kRdmVals; ++q) acc[q] = 0.0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g0 < ngroups; g0 += 4 * stride) {
+    // kRdmBatch groups are loaded at once (independent loads in flight), two
+    // batches are summed in FP32, then added to the FP64 accumulators (the FP64
+    // pipe is narrow on this part: one FP64 add per value per 2 batches)
+    for (uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g0 < ngroups; g0 += 2 * kRdmBatch * stride) {
         T a[kRdmVals];
 #pragma unroll
         for (int q = 0; q < kRdmVals; ++q) a[q] = (T)0;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-            const uint64_t g = g0 + rr * stride;
-            if (g >= ngroups) break;
-            // insert zero bits at bl and bh
-            const uint64_t base = (g & mlo) | ((g & mmid) << 1) | ((g & ~(mlo | mmid)) << 2);
-            C x[4];
+        for (int half = 0; half < 2; ++half) {
+            C x[kRdmBatch][4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) x[v] = psi[base | ((uint64_t)(v >> 1) << bh) | ((uint64_t)(v & 1) << bl)];
+            for (int rr = 0; rr < kRdmBatch; ++rr) {
+                const uint64_t g = g0 + (uint64_t)(half * kRdmBatch + rr) * stride;
+                // insert zero bits at bl and bh
+                const uint64_t base = (g & mlo) | ((g & mmid) << 1) | ((g & ~(mlo | mmid)) << 2);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) a[v] += x[v].x * x[v].x + x[v].y * x[v].y;
-            int q = 4;
-#pragma unroll
-            for (int v1 = 0; v1 < 4; ++v1)
-#pragma unroll
-                for (int v2 = v1 + 1; v2 < 4; ++v2) {  // x[v1] conj(x[v2])
-                    a[q] += x[v1].x * x[v2].x + x[v1].y * x[v2].y;
-                    a[q + 1] += x[v1].y * x[v2].x - x[v1].x * x[v2].y;
-                    q += 2;
+                for (int v = 0; v < 4; ++v) {
+                    x[rr][v].x = (T)0;
+                    x[rr][v].y = (T)0;
+                    if (g < ngroups) x[rr][v] = psi[base | ((uint64_t)(v >> 1) << bh) | ((uint64_t)(v & 1) << bl)];
                 }
+            }
+#pragma unroll
+            for (int rr = 0; rr < kRdmBatch; ++rr) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) a[v] += x[rr][v].x * x[rr][v].x + x[rr][v].y * x[rr][v].y;
+                int q = 4;
+#pragma unroll
+                for (int v1 = 0; v1 < 4; ++v1)
+#pragma unroll
+                    for (int v2 = v1 + 1; v2 < 4; ++v2) {  // x[v1] conj(x[v2])
+                        a[q] += x[rr][v1].x * x[rr][v2].x + x[rr][v1].y * x[rr][v2].y;
+                        a[q + 1] += x[rr][v1].y * x[rr][v2].x - x[rr][v1].x * x[rr][v2].y;
+                        q += 2;
+                    }
+            }
         }
 #pragma unroll
         for (int q = 0; q < kRdmVals; ++q) acc[q] += (double)a[q];
