@@ -24,9 +24,10 @@ namespace {
 // Asynchronous bond entropy: the Gram product rho = psi_A psi_A^dag runs on the
 // caller's stream (psi may be overwritten as soon as it is enqueued); the
 // Hermitian eigen-solve and the entropy sum run on a lowest-priority
-// non-blocking side stream, driven by a worker thread of the handle because
-// the eigen-solver blocks its host thread.  Two rho buffers (slots) let the
-// caller run ahead by up to two measurements.
+// non-blocking stream of one of two result slots.  With the library solver
+// each slot has its own solver handle, stream and worker thread (the solver
+// blocks its host thread), so two measurements can be in flight at once; with
+// this library's solver the calling thread enqueues everything itself.
 struct AsyncJob {
     int slot;
     int n;
@@ -35,35 +36,34 @@ struct AsyncJob {
 };
 
 struct AsyncMeas {
-    std::thread worker;
+    std::thread worker[2];
     std::mutex mu;
     std::condition_variable cv;
     bool stop = false;
-    bool busy[2] = {false, false};  // slot holds a job not yet finished
-    std::vector<AsyncJob> queue;
+    bool busy[2] = {false, false};    // slot holds a measurement not yet finished
+    bool queued[2] = {false, false};  // library mode: slot's job waits for its worker
+    AsyncJob job[2] = {};             // the job a slot holds
     int next_slot = 0;
-    osmps_status err = OSMPS_OK;    // first failure of a job, returned by the wait
-    int64_t launches = 0;           // kernels launched on the side stream
-    cudaStream_t side = nullptr;
+    osmps_status err = OSMPS_OK;      // first failure of a job, returned by the wait
+    int64_t launches = 0;             // kernels launched by the workers
+    cudaStream_t ss[2] = {nullptr, nullptr};  // per-slot streams (lowest priority, non-blocking)
     cudaEvent_t ready[2] = {nullptr, nullptr};
+    cudaEvent_t done[2] = {nullptr, nullptr};
     void *rho[2] = {nullptr, nullptr};
     size_t rho_bytes[2] = {0, 0};
     double *lam[2] = {nullptr, nullptr};   // lambda (n) and S on the device
     size_t lam_bytes[2] = {0, 0};
     double *host[2] = {nullptr, nullptr};  // pinned staging of lambda and S
     size_t host_bytes[2] = {0, 0};
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    // own eigen-solver (osmps_ed_set_async_eigensolver > 0): every step of a
-    // measurement is enqueued by the calling thread on the slot's stream
+    void *sh[2] = {nullptr, nullptr};      // library mode: per-slot solver handles
+    void *ws[2] = {nullptr, nullptr};      // library mode: per-slot solver workspaces
+    size_t ws_bytes[2] = {0, 0};
+    // own eigen-solver (osmps_ed_set_async_eigensolver > 0)
     int own_G = 0;                           // CTAs of the cooperative reduction; 0 = library solver
-    cudaStream_t ss[2] = {nullptr, nullptr};  // per-slot streams (lowest priority, non-blocking)
-    cudaEvent_t done[2] = {nullptr, nullptr};
     void *tws[2] = {nullptr, nullptr};
     size_t tws_bytes[2] = {0, 0};
     int *err_dev = nullptr;                  // 2 ints: bounded waits of the reduction gave up
     int *err_host = nullptr;                 // pinned copies
-    AsyncJob job[2] = {};                    // the job a slot holds in this mode
 };
 
 }  // namespace
@@ -358,42 +358,48 @@ void destroy_handle(Handle *h) {
     dev_free(h, h->lam_dev, 0);
 }
 
-void async_worker(Handle *h, AsyncMeas *am) {
+// Library mode: the worker of slot sl solves the slot's queued job.
+void async_worker(Handle *h, AsyncMeas *am, int sl) {
     cudaSetDevice(h->device);
     std::unique_lock<std::mutex> lock(am->mu);
     for (;;) {
-        am->cv.wait(lock, [am] { return am->stop || !am->queue.empty(); });
-        if (am->queue.empty()) return;  // stop requested and nothing left
-        const AsyncJob job = am->queue.front();
-        am->queue.erase(am->queue.begin());
-        const int sl = job.slot, n = job.n;
-        void *ws = am->ws;
-        size_t ws_bytes = am->ws_bytes;
+        am->cv.wait(lock, [am, sl] { return am->stop || am->queued[sl]; });
+        if (!am->queued[sl]) return;  // stop requested and nothing left
+        am->queued[sl] = false;
+        const AsyncJob job = am->job[sl];
+        const int n = job.n;
+        void *ws = am->ws[sl];
+        size_t ws_bytes = am->ws_bytes[sl];
         int64_t launches = 0;
+        cudaStream_t st = am->ss[sl];
         lock.unlock();
-        osmps_status st = from_cuda(cudaStreamWaitEvent(am->side, am->ready[sl], 0));
-        if (st == OSMPS_OK)
-            st = schmidt_eig_on(h, am->side, &ws, &ws_bytes, false, &launches, am->rho[sl], n, am->lam[sl],
+        osmps_status rs = from_cuda(cudaStreamWaitEvent(st, am->ready[sl], 0));
+        if (rs == OSMPS_OK && am->sh[sl] == nullptr) {
+            am->sh[sl] = solver_handle_new();
+            if (am->sh[sl] == nullptr) rs = OSMPS_EUNSUPPORTED;
+        }
+        if (rs == OSMPS_OK)
+            rs = schmidt_eig_on(h, st, am->sh[sl], &ws, &ws_bytes, false, &launches, am->rho[sl], n, am->lam[sl],
                                 am->lam[sl] + n);
-        if (st == OSMPS_OK)
-            st = from_cuda(cudaMemcpyAsync(am->host[sl], am->lam[sl], sizeof(double) * (n + 1),
-                                           cudaMemcpyDeviceToHost, am->side));
-        if (st == OSMPS_OK) st = from_cuda(cudaStreamSynchronize(am->side));
-        if (st == OSMPS_OK) {
+        if (rs == OSMPS_OK)
+            rs = from_cuda(cudaMemcpyAsync(am->host[sl], am->lam[sl], sizeof(double) * (n + 1),
+                                           cudaMemcpyDeviceToHost, st));
+        if (rs == OSMPS_OK) rs = from_cuda(cudaStreamSynchronize(st));
+        if (rs == OSMPS_OK) {
             if (job.lambda_host) std::memcpy(job.lambda_host, am->host[sl], sizeof(double) * n);
             if (job.S_host) *job.S_host = am->host[sl][n];
         }
         lock.lock();
-        am->ws = ws;
-        am->ws_bytes = ws_bytes;
+        am->ws[sl] = ws;
+        am->ws_bytes[sl] = ws_bytes;
         am->launches += launches;
-        if (st != OSMPS_OK && am->err == OSMPS_OK) am->err = st;
+        if (rs != OSMPS_OK && am->err == OSMPS_OK) am->err = rs;
         am->busy[sl] = false;
         am->cv.notify_all();
     }
 }
 
-// Stops the worker after its queued jobs and frees the side resources.
+// Stops the workers after their queued jobs and frees the slot resources.
 void destroy_async(AsyncMeas *am) {
     if (am == nullptr) return;
     {
@@ -401,20 +407,18 @@ void destroy_async(AsyncMeas *am) {
         am->stop = true;
     }
     am->cv.notify_all();
-    if (am->worker.joinable()) am->worker.join();
-    if (am->side) cudaStreamSynchronize(am->side);
+    for (int i = 0; i < 2; ++i)
+        if (am->worker[i].joinable()) am->worker[i].join();
     for (int i = 0; i < 2; ++i) {
+        if (am->ss[i]) cudaStreamSynchronize(am->ss[i]);
         if (am->ready[i]) cudaEventDestroy(am->ready[i]);
+        if (am->done[i]) cudaEventDestroy(am->done[i]);
         if (am->rho[i]) cudaFree(am->rho[i]);
         if (am->lam[i]) cudaFree(am->lam[i]);
         if (am->host[i]) cudaFreeHost(am->host[i]);
-    }
-    if (am->ws) cudaFree(am->ws);
-    if (am->side) cudaStreamDestroy(am->side);
-    for (int i = 0; i < 2; ++i) {
-        if (am->ss[i]) cudaStreamSynchronize(am->ss[i]);
-        if (am->done[i]) cudaEventDestroy(am->done[i]);
+        if (am->ws[i]) cudaFree(am->ws[i]);
         if (am->tws[i]) cudaFree(am->tws[i]);
+        solver_handle_free(am->sh[i]);
         if (am->ss[i]) cudaStreamDestroy(am->ss[i]);
     }
     if (am->err_dev) cudaFree(am->err_dev);
@@ -422,16 +426,10 @@ void destroy_async(AsyncMeas *am) {
     delete am;
 }
 
-// Streams, events and error words of the own-solver mode (created once).
+// Error words of the own-solver mode (created once).
 osmps_status ensure_own_mode(AsyncMeas *am) {
     if (am->err_dev != nullptr) return OSMPS_OK;
-    int least = 0, greatest = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaStreamCreateWithPriority(&am->ss[i], cudaStreamNonBlocking, least);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&am->done[i], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&am->err_host, 2 * sizeof(int));
+    cudaError_t e = cudaMallocHost((void **)&am->err_host, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&am->err_dev, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(am->err_dev, 0, 2 * sizeof(int));
     if (e != cudaSuccess) {
@@ -465,15 +463,18 @@ osmps_status create_async(Handle *h, AsyncMeas **out) {
     if (am == nullptr) return OSMPS_ENOMEM;
     int least = 0, greatest = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&am->side, cudaStreamNonBlocking, least);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&am->ready[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithPriority(&am->ss[i], cudaStreamNonBlocking, least);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&am->ready[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&am->done[i], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         destroy_async(am);
         return from_cuda(e);
     }
     try {
-        am->worker = std::thread(async_worker, h, am);
+        for (int i = 0; i < 2; ++i) am->worker[i] = std::thread(async_worker, h, am, i);
     } catch (...) {
         destroy_async(am);
         return OSMPS_ENOMEM;
@@ -1047,7 +1048,8 @@ osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int
     {
         std::lock_guard<std::mutex> lock(am->mu);
         am->busy[sl] = true;
-        am->queue.push_back(AsyncJob{sl, nn, S, lambda});
+        am->queued[sl] = true;
+        am->job[sl] = AsyncJob{sl, nn, S, lambda};
         am->next_slot = sl ^ 1;
     }
     am->cv.notify_all();

@@ -138,8 +138,11 @@ size_t trd_workspace_bytes(int n, int prec, int G);
 cudaError_t trd_eigvals(const TrdRun &run, void *rho, int n, double **w);
 
 // the same on a given stream and workspace (tracked: the workspace counts in the handle's owned bytes)
-osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void **ws, size_t *ws_bytes, bool tracked,
+// solver: a handle from solver_handle_new, or null for the process-wide one (serialised)
+osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void **ws, size_t *ws_bytes, bool tracked,
                             int64_t *launches, void *rho, int n, double *lambda_dev, double *S_dev);
+void *solver_handle_new();        // null if the library solver cannot be loaded
+void solver_handle_free(void *solver);
 
 // Device memory owned by a handle.
 struct Handle {

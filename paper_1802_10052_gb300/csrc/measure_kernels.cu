@@ -464,6 +464,7 @@ struct SolverLib {
     cusolverDnHandle_t handle = nullptr;
     decltype(&cusolverDnCreate) create = nullptr;
     decltype(&cusolverDnSetStream) set_stream = nullptr;
+    decltype(&cusolverDnDestroy) destroy = nullptr;
     decltype(&cusolverDnZheevd_bufferSize) z_bufsize = nullptr;
     decltype(&cusolverDnZheevd) z_eig = nullptr;
     decltype(&cusolverDnCheevd_bufferSize) c_bufsize = nullptr;
@@ -482,6 +483,7 @@ static bool load_solver() {
     if (!g_solver.so) return false;
     g_solver.create = (decltype(g_solver.create))dlsym(g_solver.so, "cusolverDnCreate");
     g_solver.set_stream = (decltype(g_solver.set_stream))dlsym(g_solver.so, "cusolverDnSetStream");
+    g_solver.destroy = (decltype(g_solver.destroy))dlsym(g_solver.so, "cusolverDnDestroy");
     g_solver.z_bufsize = (decltype(g_solver.z_bufsize))dlsym(g_solver.so, "cusolverDnZheevd_bufferSize");
     g_solver.z_eig = (decltype(g_solver.z_eig))dlsym(g_solver.so, "cusolverDnZheevd");
     g_solver.c_bufsize = (decltype(g_solver.c_bufsize))dlsym(g_solver.so, "cusolverDnCheevd_bufferSize");
@@ -520,20 +522,38 @@ __global__ void entropy_kernel(const T *w, int n, double *lambda, double *S) {
 // synchronous one never share it at the same time.
 static std::mutex g_solver_mu;
 
-osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void **ws_p, size_t *ws_bytes_p, bool tracked,
-                            int64_t *launches, void *rho, int n, double *lambda_dev, double *S_dev) {
+void *solver_handle_new() {
     std::lock_guard<std::mutex> lock(g_solver_mu);
-    if (!load_solver()) return OSMPS_EUNSUPPORTED;
-    if (g_solver.set_stream(g_solver.handle, stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+    if (!load_solver() || g_solver.destroy == nullptr) return nullptr;
+    cusolverDnHandle_t sh = nullptr;
+    if (g_solver.create(&sh) != CUSOLVER_STATUS_SUCCESS) return nullptr;
+    return sh;
+}
+
+void solver_handle_free(void *solver) {
+    if (solver != nullptr && g_solver.destroy != nullptr) g_solver.destroy((cusolverDnHandle_t)solver);
+}
+
+osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void **ws_p, size_t *ws_bytes_p,
+                            bool tracked, int64_t *launches, void *rho, int n, double *lambda_dev, double *S_dev) {
+    // the process-wide handle is shared: hold the lock for the whole call; a
+    // caller's own handle needs none (the library was loaded when it was made)
+    std::unique_lock<std::mutex> lock(g_solver_mu, std::defer_lock);
+    if (solver == nullptr) {
+        lock.lock();
+        if (!load_solver()) return OSMPS_EUNSUPPORTED;
+    }
+    const cusolverDnHandle_t hs = solver ? (cusolverDnHandle_t)solver : g_solver.handle;
+    if (g_solver.set_stream(hs, stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
     int lwork = 0;
     const bool dbl = (h->prec == OSMPS_FP64);
     cusolverStatus_t st;
     const size_t wbytes = (dbl ? sizeof(double) : sizeof(float)) * (size_t)n;
     if (dbl)
-        st = g_solver.z_bufsize(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+        st = g_solver.z_bufsize(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
                                 (const cuDoubleComplex *)rho, n, (const double *)nullptr, &lwork);
     else
-        st = g_solver.c_bufsize(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+        st = g_solver.c_bufsize(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
                                 (const cuComplex *)rho, n, (const float *)nullptr, &lwork);
     if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
     const size_t need = (size_t)lwork * (dbl ? sizeof(cuDoubleComplex) : sizeof(cuComplex)) + wbytes + 64;
@@ -561,10 +581,10 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void **ws_p, size_t 
     void *wvals = ws + 16;
     void *work = ws + 16 + ((wbytes + 15) & ~(size_t)15);
     if (dbl)
-        st = g_solver.z_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
+        st = g_solver.z_eig(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
                             (cuDoubleComplex *)rho, n, (double *)wvals, (cuDoubleComplex *)work, lwork, info);
     else
-        st = g_solver.c_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n, (cuComplex *)rho,
+        st = g_solver.c_eig(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n, (cuComplex *)rho,
                             n, (float *)wvals, (cuComplex *)work, lwork, info);
     if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
     if (dbl)
@@ -581,8 +601,8 @@ cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *
 }
 
 osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev) {
-    return schmidt_eig_on(h, h->stream, &h->solver_ws, &h->solver_ws_bytes, true, &h->launches, rho, n, lambda_dev,
-                          S_dev);
+    return schmidt_eig_on(h, h->stream, nullptr, &h->solver_ws, &h->solver_ws_bytes, true, &h->launches, rho, n,
+                          lambda_dev, S_dev);
 }
 
 }  // namespace osmps

@@ -19,7 +19,8 @@ namespace rdm {
 constexpr int kRdmThreads = 256;
 constexpr int kRdmBlocks = 48;  // blocks per pair
 constexpr int kRdmVals = 16;    // 4 diagonal + 6 (re, im) upper entries
-constexpr int kRdmBatch = 8;    // amplitude quadruples loaded together per thread
+constexpr int kRdmBatch = 4;    // amplitude quadruples loaded together per thread
+constexpr int kRdmRuns = 4;     // batches summed in FP32 before the FP64 accumulators
 
 template <typename T> struct Cr;
 template <> struct Cr<float> { typedef float2 C; };
@@ -36,7 +37,7 @@ __device__ __forceinline__ void pair_sites(int p, int L, int &i, int &j) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRdmThreads) pair_rdm_kernel(const typename Cr<T>::C *psi, int L, double *partials) {
+__global__ void __launch_bounds__(kRdmThreads, sizeof(T) == 4 ? 2 : 1) pair_rdm_kernel(const typename Cr<T>::C *psi, int L, double *partials) {
     typedef typename Cr<T>::C C;
     int si, sj;
     pair_sites(blockIdx.y, L, si, sj);
@@ -48,19 +49,20 @@ __global__ void __launch_bounds__(kRdmThreads) pair_rdm_kernel(const typename Cr
 #pragma unroll
     for (int q = 0; q < kRdmVals; ++q) acc[q] = 0.0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // kRdmBatch groups are loaded at once (independent loads in flight), two
-    // batches are summed in FP32, then added to the FP64 accumulators (the FP64
-    // pipe is narrow on this part: one FP64 add per value per 2 batches)
-    for (uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g0 < ngroups; g0 += 2 * kRdmBatch * stride) {
+    // kRdmBatch groups are loaded at once (independent loads in flight),
+    // kRdmRuns batches are summed in FP32, then added to the FP64 accumulators
+    // (the FP64 pipe is narrow on this part: one FP64 add per value per run)
+    for (uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g0 < ngroups;
+         g0 += (uint64_t)kRdmRuns * kRdmBatch * stride) {
         T a[kRdmVals];
 #pragma unroll
         for (int q = 0; q < kRdmVals; ++q) a[q] = (T)0;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int run = 0; run < kRdmRuns; ++run) {
             C x[kRdmBatch][4];
 #pragma unroll
             for (int rr = 0; rr < kRdmBatch; ++rr) {
-                const uint64_t g = g0 + (uint64_t)(half * kRdmBatch + rr) * stride;
+                const uint64_t g = g0 + (uint64_t)(run * kRdmBatch + rr) * stride;
                 // insert zero bits at bl and bh
                 const uint64_t base = (g & mlo) | ((g & mmid) << 1) | ((g & ~(mlo | mmid)) << 2);
 #pragma unroll
