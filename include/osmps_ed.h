@@ -277,8 +277,9 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
  * measures taken along a time evolution).  The Gram product rho =
  * psi_A psi_A^dag is enqueued on the handle's stream, so psi may be changed
  * by work enqueued after this call; the eigen-solve and the entropy then run
- * on a lowest-priority non-blocking stream of the handle, driven by a worker
- * thread of the handle (the eigen-solver blocks its host thread).  Results go
+ * on the lowest-priority non-blocking stream of one of two result slots of
+ * the handle; with the library solver each slot also has its own solver
+ * handle and worker thread (the solver blocks its host thread).  Results go
  * to the host pointers S (one double) and lambda (2^min(cut, L-cut) doubles,
  * or NULL), which the caller keeps valid and does not read until
  * osmps_ed_measure_wait returns.  Two measurements may be outstanding; a

@@ -7,8 +7,9 @@
 // One launch covers all L(L-1)/2 pairs (blockIdx.y = pair).  A thread takes
 // groups of the four amplitudes that differ only in the pair's two bits (the
 // group index with two zero bits inserted) and accumulates the Hermitian
-// 4 x 4 outer product x x^H: 4 real diagonal and 6 complex upper entries, FP32
-// per thread and chunk, FP64 across chunks, threads and blocks (fixed order).
+// 4 x 4 outer product x x^H: 4 real diagonal and 6 complex upper entries,
+// compensated sums in the working precision per thread, FP64 across threads
+// and blocks (fixed order).
 #include <cuda_runtime.h>
 
 #include "ed_internal.h"
@@ -45,13 +46,15 @@ __global__ void __launch_bounds__(kRdmThreads, sizeof(T) == 4 ? 2 : 1) pair_rdm_
     const uint64_t ngroups = (1ull << L) >> 2;
     const uint64_t mlo = (1ull << bl) - 1ull;          // bits below bl
     const uint64_t mmid = ((1ull << (bh - 1)) - 1ull) & ~mlo;  // group bits that land between bl and bh
-    double acc[kRdmVals];
+    // per-thread sums: compensated (Kahan) in the working precision, so that
+    // the long per-thread runs keep full accuracy without FP64 work in the
+    // loop (the FP64 pipe of this part is narrow); FP64 from the thread sums on
+    T acc[kRdmVals], comp[kRdmVals];
 #pragma unroll
-    for (int q = 0; q < kRdmVals; ++q) acc[q] = 0.0;
+    for (int q = 0; q < kRdmVals; ++q) acc[q] = comp[q] = (T)0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     // kRdmBatch groups are loaded at once (independent loads in flight),
-    // kRdmRuns batches are summed in FP32, then added to the FP64 accumulators
-    // (the FP64 pipe is narrow on this part: one FP64 add per value per run)
+    // kRdmRuns batches are summed plainly, then added to the compensated sums
     for (uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g0 < ngroups;
          g0 += (uint64_t)kRdmRuns * kRdmBatch * stride) {
         T a[kRdmVals];
@@ -88,12 +91,17 @@ __global__ void __launch_bounds__(kRdmThreads, sizeof(T) == 4 ? 2 : 1) pair_rdm_
             }
         }
 #pragma unroll
-        for (int q = 0; q < kRdmVals; ++q) acc[q] += (double)a[q];
+        for (int q = 0; q < kRdmVals; ++q) {
+            const T y = a[q] - comp[q];
+            const T t = acc[q] + y;
+            comp[q] = (t - acc[q]) - y;
+            acc[q] = t;
+        }
     }
     __shared__ double red[kRdmVals][kRdmThreads / 32];
 #pragma unroll
     for (int q = 0; q < kRdmVals; ++q) {
-        double v = acc[q];
+        double v = (double)acc[q] - (double)comp[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;

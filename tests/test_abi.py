@@ -60,6 +60,13 @@ def test_strerror_and_host_side_argument_checks():
     assert lib.osmps_ed_destroy(None) == B.OSMPS_OK
     assert lib.osmps_ed_apply_H(None, None, None) == B.OSMPS_EINVAL
     assert lib.osmps_ed_krylov_evolve(None, None, 0.1, 1, 20, 0.0, None) == B.OSMPS_EINVAL
+    # scheduling entry points: a null handle is rejected before any CUDA call
+    S = C.c_double()
+    assert lib.osmps_ed_schmidt_entropy_async(None, None, -1, C.byref(S), None) == B.OSMPS_EINVAL
+    assert lib.osmps_ed_measure_wait(None) == B.OSMPS_EINVAL
+    assert lib.osmps_ed_set_async_eigensolver(None, 16) == B.OSMPS_EINVAL
+    assert lib.osmps_ed_set_sm_count(None, 8) == B.OSMPS_EINVAL
+    assert lib.osmps_ed_set_prefetch(None, 1) == B.OSMPS_EINVAL
 
 
 def test_batch_host_side_argument_checks():

@@ -108,3 +108,22 @@ def test_apply_H_full_size_sampled_rows(L, prec):
     assert rel(got, ref) < (1e-13 if prec == "fp64" else 1e-6)
     del out, x, c
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("L", [13, 20, 24])
+def test_prefetch_and_sm_count_do_not_change_the_product(L, prec):
+    """The L2 prefetch distance and the grid size schedule memory traffic only:
+    H.psi is bit-identical across them (no reduction enters the output)."""
+    c = chain_for(L, [1.0 / r ** 1.5 for r in range(1, L)], [0.8] * L, prec)
+    x = to_dev(si.gaussian_state(L, 3 * L), prec)
+    ref = c.new_state()
+    c.set_prefetch(0)
+    c.apply_H(x, ref)
+    out = c.new_state()
+    for pf, nsm in ((1, 0), (2, 0), (3, 0), (1, 96), (0, 17)):
+        c.set_prefetch(pf)
+        c.set_sm_count(nsm)
+        c.apply_H(x, out)
+        assert torch.equal(out, ref), (pf, nsm)
+    c.close()
