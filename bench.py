@@ -140,6 +140,26 @@ def traffic_record():
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (replicas: one independent quench per rank)
+# ---------------------------------------------------------------------------
+def max_over_ranks(value, world, device):
+    """The job's time is its slowest rank's: max of a per-rank scalar over all ranks."""
+    if world <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms_max, steps, world):
+    """Seconds of wall time per unit of simulated time of the whole job: each of the
+    world ranks advances its own replica by SIM_TIME_PER_STEP per step."""
+    return (ms_max / 1000.0) / (SIM_TIME_PER_STEP * steps * world)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world):
@@ -196,14 +216,9 @@ def run_ours(args, rank, world):
     chain.timing_enable(False)
     hp_ms, hp_calls = chain.timing_read(reset=True)
     launches = (chain_launches(chain) - launches0) // max(args.steps, 1)
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     ms_per_step = ms / args.steps
-    sim_time = SIM_TIME_PER_STEP * args.steps * world
-    value = (ms / 1000.0) / sim_time
+    value = job_value(ms, args.steps, world)
 
     # error of this configuration against the FP64 form (same GPU, same horizon)
     out = {"ms_per_step": ms_per_step, "value": value, "clocks": ck, "launches_per_step": launches,
