@@ -517,6 +517,17 @@ __global__ void entropy_kernel(const T *w, int n, double *lambda, double *S) {
     }
 }
 
+// flag = 1 when the library solver reported a failure (info != 0) or returned
+// a non-finite eigenvalue
+template <typename T>
+__global__ void eig_check_kernel(const int *info, const T *w, int n, int *flag) {
+    int bad = (threadIdx.x == 0 && *info != 0) ? 1 : 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (!isfinite((double)w[i])) bad = 1;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) *flag = bad;
+}
+
 // One cuSOLVER handle serves the process; its use (and its lazy loading) is
 // serialised, so that an asynchronous measurement on a worker thread and a
 // synchronous one never share it at the same time.
@@ -556,7 +567,17 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void *
         st = g_solver.c_bufsize(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
                                 (const cuComplex *)rho, n, (const float *)nullptr, &lwork);
     if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
-    const size_t need = (size_t)lwork * (dbl ? sizeof(cuDoubleComplex) : sizeof(cuComplex)) + wbytes + 64;
+    // workspace: info and the failure flag, eigenvalues, the solver's work
+    // array, a copy of rho and the workspace of this library's reduction,
+    // which takes over when the library solver fails on the copy
+    const size_t cs = dbl ? sizeof(cuDoubleComplex) : sizeof(cuComplex);
+    const int G = trd_ctas(n, h->prec, h->nsm, h->device);
+    const size_t o_work = 16 + ((wbytes + 15) & ~(size_t)15);
+    const size_t o_copy = o_work + (((size_t)lwork * cs + 255) & ~(size_t)255);
+    const size_t copy_bytes = G > 0 ? (size_t)n * n * cs : 0;
+    const size_t o_trd = o_copy + ((copy_bytes + 255) & ~(size_t)255);
+    const size_t trd_bytes = G > 0 ? trd_workspace_bytes(n, h->prec, G) : 0;
+    const size_t need = o_trd + trd_bytes + 64;
     if (need > *ws_bytes_p) {
         if (*ws_p) {
             if (tracked)
@@ -578,8 +599,11 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void *
     }
     char *ws = (char *)*ws_p;
     int *info = (int *)ws;
+    int *flag = info + 1;
     void *wvals = ws + 16;
-    void *work = ws + 16 + ((wbytes + 15) & ~(size_t)15);
+    void *work = ws + o_work;
+    if (copy_bytes > 0 && cudaMemcpyAsync(ws + o_copy, rho, copy_bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+        return OSMPS_ECUDA;
     if (dbl)
         st = g_solver.z_eig(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
                             (cuDoubleComplex *)rho, n, (double *)wvals, (cuDoubleComplex *)work, lwork, info);
@@ -588,11 +612,35 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void *
                             n, (float *)wvals, (cuComplex *)work, lwork, info);
     if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
     if (dbl)
-        entropy_kernel<double><<<1, 1024, 0, stream>>>((const double *)wvals, n, lambda_dev, S_dev);
+        eig_check_kernel<double><<<1, 1024, 0, stream>>>(info, (const double *)wvals, n, flag);
     else
-        entropy_kernel<float><<<1, 1024, 0, stream>>>((const float *)wvals, n, lambda_dev, S_dev);
+        eig_check_kernel<float><<<1, 1024, 0, stream>>>(info, (const float *)wvals, n, flag);
     *launches += 1;
-    return cudaGetLastError() == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
+    int bad = 0;
+    if (cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return OSMPS_ECUDA;
+    if (bad == 0) {
+        if (dbl)
+            entropy_kernel<double><<<1, 1024, 0, stream>>>((const double *)wvals, n, lambda_dev, S_dev);
+        else
+            entropy_kernel<float><<<1, 1024, 0, stream>>>((const float *)wvals, n, lambda_dev, S_dev);
+        *launches += 1;
+        return cudaGetLastError() == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
+    }
+    // the library solver failed (seen on nearly rank-one complex64 matrices):
+    // this library's reduction on the saved copy of rho
+    if (G == 0) return OSMPS_ECUDA;
+    if (cudaMemsetAsync(flag, 0, sizeof(int), stream) != cudaSuccess) return OSMPS_ECUDA;
+    TrdRun run{h->prec, h->device, stream, G, ws + o_trd, trd_bytes, flag, launches};
+    double *w = nullptr;
+    if (trd_eigvals(run, ws + o_copy, n, &w) != cudaSuccess) return OSMPS_ECUDA;
+    entropy_kernel<double><<<1, 1024, 0, stream>>>(w, n, lambda_dev, S_dev);
+    *launches += 1;
+    if (cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return OSMPS_ECUDA;
+    return bad == 0 ? OSMPS_OK : OSMPS_ETIMEOUT;
 }
 
 cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *lambda_dev, double *S_dev) {

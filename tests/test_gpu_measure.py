@@ -3,6 +3,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 import seeded_inputs as si
 from oracle import ed_oracle as O
@@ -132,3 +133,27 @@ def test_tensor_core_gram_product_state_and_ghz():
     S, lam = c.schmidt_entropy(g, spectrum=True)
     assert abs(S - math.log(2.0)) < 1e-6
     np.testing.assert_allclose(lam[:2], 0.5, atol=1e-7)
+
+
+def test_mixed_spectrum_of_nearly_rank_one_state_L24():
+    """L = 24 quench state at t = 0.1 (FP64 evolution, rounded to complex64): rho
+    is nearly rank one (4094 eigenvalues below 1e-7).  The complex64 spectrum
+    must be finite and sum to one (the library solver has returned non-finite
+    values on such a matrix; then this library's reduction takes over), and S
+    must agree with the FP64 form to the complex64 noise floor of the small
+    eigenvalues (absolute 2e-5, measured 5e-6)."""
+    L = 24
+    c64 = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="fp64")
+    x = c64.new_state()
+    c64.init_basis_state(x, 0)
+    c64.krylov_evolve(x, 0.01, 10, 20)
+    S64 = c64.schmidt_entropy(x)
+    y = x.to(torch.complex64)
+    del x, c64
+    torch.cuda.empty_cache()
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    S, lam = c.schmidt_entropy(y, spectrum=True)
+    assert np.all(np.isfinite(lam))
+    assert abs(lam.sum() - 1.0) < 1e-5
+    assert abs(lam[0] - (1.0 - lam[1:].sum())) < 1e-5
+    assert abs(S - S64) < 2e-5
