@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <vector>
 
 #include "ed_internal.h"
 
@@ -469,6 +470,11 @@ struct SolverLib {
     decltype(&cusolverDnZheevd) z_eig = nullptr;
     decltype(&cusolverDnCheevd_bufferSize) c_bufsize = nullptr;
     decltype(&cusolverDnCheevd) c_eig = nullptr;
+    // 64-bit API (workspace sizes beyond 2^31 elements, e.g. n = 32768)
+    decltype(&cusolverDnCreateParams) create_params = nullptr;
+    decltype(&cusolverDnXsyevd_bufferSize) x_bufsize = nullptr;
+    decltype(&cusolverDnXsyevd) x_eig = nullptr;
+    cusolverDnParams_t params = nullptr;  // default options, read-only after creation
 };
 static SolverLib g_solver;
 
@@ -492,6 +498,12 @@ static bool load_solver() {
         !g_solver.c_eig)
         return false;
     if (g_solver.create(&g_solver.handle) != CUSOLVER_STATUS_SUCCESS) return false;
+    g_solver.create_params = (decltype(g_solver.create_params))dlsym(g_solver.so, "cusolverDnCreateParams");
+    g_solver.x_bufsize = (decltype(g_solver.x_bufsize))dlsym(g_solver.so, "cusolverDnXsyevd_bufferSize");
+    g_solver.x_eig = (decltype(g_solver.x_eig))dlsym(g_solver.so, "cusolverDnXsyevd");
+    if (!g_solver.create_params || !g_solver.x_bufsize || !g_solver.x_eig ||
+        g_solver.create_params(&g_solver.params) != CUSOLVER_STATUS_SUCCESS)
+        g_solver.params = nullptr;
     g_solver.ok = true;
     return true;
 }
@@ -533,6 +545,35 @@ __global__ void eig_check_kernel(const int *info, const T *w, int n, int *flag) 
 // synchronous one never share it at the same time.
 static std::mutex g_solver_mu;
 
+#define CKS_(expr)                          \
+    do {                                    \
+        const osmps_status _s = (expr);     \
+        if (_s != OSMPS_OK) return _s;      \
+    } while (0)
+
+// Device buffer of at least `need` bytes in *ws_p (counted in the handle's bytes when tracked).
+static osmps_status grow_ws(Handle *h, void **ws_p, size_t *ws_bytes_p, bool tracked, size_t need) {
+    if (need <= *ws_bytes_p) return OSMPS_OK;
+    if (*ws_p) {
+        if (tracked)
+            dev_free(h, *ws_p, *ws_bytes_p);
+        else
+            cudaFree(*ws_p);
+    }
+    *ws_p = nullptr;
+    *ws_bytes_p = 0;
+    cudaError_t err = cudaSuccess;
+    if (tracked) {
+        *ws_p = dev_alloc(h, need, &err);
+    } else if ((err = cudaMalloc(ws_p, need)) != cudaSuccess) {
+        cudaGetLastError();
+        *ws_p = nullptr;
+    }
+    if (err != cudaSuccess) return OSMPS_ENOMEM;
+    *ws_bytes_p = need;
+    return OSMPS_OK;
+}
+
 void *solver_handle_new() {
     std::lock_guard<std::mutex> lock(g_solver_mu);
     if (!load_solver() || g_solver.destroy == nullptr) return nullptr;
@@ -556,47 +597,41 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void *
     }
     const cusolverDnHandle_t hs = solver ? (cusolverDnHandle_t)solver : g_solver.handle;
     if (g_solver.set_stream(hs, stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
-    int lwork = 0;
     const bool dbl = (h->prec == OSMPS_FP64);
-    cusolverStatus_t st;
+    const bool x64 = g_solver.params != nullptr;
+    const cudaDataType ta = dbl ? CUDA_C_64F : CUDA_C_32F, tw = dbl ? CUDA_R_64F : CUDA_R_32F;
+    const size_t cs = dbl ? sizeof(cuDoubleComplex) : sizeof(cuComplex);
     const size_t wbytes = (dbl ? sizeof(double) : sizeof(float)) * (size_t)n;
-    if (dbl)
+    const size_t o_work = 16 + ((wbytes + 15) & ~(size_t)15);
+    // the size queries get real buffers: info and the eigenvalue array first
+    CKS_(grow_ws(h, ws_p, ws_bytes_p, tracked, o_work + 256));
+    cusolverStatus_t st;
+    size_t work_bytes = 0, host_bytes = 0;
+    int lwork = 0;
+    if (x64) {
+        st = g_solver.x_bufsize(hs, g_solver.params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, (int64_t)n,
+                                ta, rho, (int64_t)n, tw, (char *)*ws_p + 16, ta, &work_bytes, &host_bytes);
+    } else if (dbl) {
         st = g_solver.z_bufsize(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                (const cuDoubleComplex *)rho, n, (const double *)nullptr, &lwork);
-    else
+                                (const cuDoubleComplex *)rho, n, (const double *)((char *)*ws_p + 16), &lwork);
+        work_bytes = (size_t)lwork * cs;
+    } else {
         st = g_solver.c_bufsize(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                (const cuComplex *)rho, n, (const float *)nullptr, &lwork);
+                                (const cuComplex *)rho, n, (const float *)((char *)*ws_p + 16), &lwork);
+        work_bytes = (size_t)lwork * cs;
+    }
     if (st != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+    if (work_bytes < 256) work_bytes = 256;
     // workspace: info and the failure flag, eigenvalues, the solver's work
     // array, a copy of rho and the workspace of this library's reduction,
     // which takes over when the library solver fails on the copy
-    const size_t cs = dbl ? sizeof(cuDoubleComplex) : sizeof(cuComplex);
     const int G = trd_ctas(n, h->prec, h->nsm, h->device);
-    const size_t o_work = 16 + ((wbytes + 15) & ~(size_t)15);
-    const size_t o_copy = o_work + (((size_t)lwork * cs + 255) & ~(size_t)255);
+    const size_t o_copy = o_work + ((work_bytes + 255) & ~(size_t)255);
     const size_t copy_bytes = G > 0 ? (size_t)n * n * cs : 0;
     const size_t o_trd = o_copy + ((copy_bytes + 255) & ~(size_t)255);
     const size_t trd_bytes = G > 0 ? trd_workspace_bytes(n, h->prec, G) : 0;
-    const size_t need = o_trd + trd_bytes + 64;
-    if (need > *ws_bytes_p) {
-        if (*ws_p) {
-            if (tracked)
-                dev_free(h, *ws_p, *ws_bytes_p);
-            else
-                cudaFree(*ws_p);
-        }
-        *ws_p = nullptr;
-        *ws_bytes_p = 0;
-        cudaError_t err = cudaSuccess;
-        if (tracked) {
-            *ws_p = dev_alloc(h, need, &err);
-        } else if ((err = cudaMalloc(ws_p, need)) != cudaSuccess) {
-            cudaGetLastError();
-            *ws_p = nullptr;
-        }
-        if (err != cudaSuccess) return OSMPS_ENOMEM;
-        *ws_bytes_p = need;
-    }
+    CKS_(grow_ws(h, ws_p, ws_bytes_p, tracked, o_trd + trd_bytes + 64));
+    std::vector<char> host_ws(host_bytes > 0 ? host_bytes : 1);
     char *ws = (char *)*ws_p;
     int *info = (int *)ws;
     int *flag = info + 1;
@@ -604,7 +639,10 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void *
     void *work = ws + o_work;
     if (copy_bytes > 0 && cudaMemcpyAsync(ws + o_copy, rho, copy_bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
         return OSMPS_ECUDA;
-    if (dbl)
+    if (x64)
+        st = g_solver.x_eig(hs, g_solver.params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, (int64_t)n, ta, rho,
+                            (int64_t)n, tw, wvals, ta, work, work_bytes, host_ws.data(), host_bytes, info);
+    else if (dbl)
         st = g_solver.z_eig(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
                             (cuDoubleComplex *)rho, n, (double *)wvals, (cuDoubleComplex *)work, lwork, info);
     else
