@@ -1087,7 +1087,7 @@ osmps_status osmps_ed_measure_wait(osmps_ed_t *ed) {
 // ---------------------------------------------------------------------------
 // Adjoint gradient of a final energy (see include/osmps_ed.h)
 // ---------------------------------------------------------------------------
-osmps_status osmps_ed_adjoint_grad(osmps_ed_t *ed, const void *psi0, int nsteps, double dt, const double *h_steps,
+static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nsteps, double dt, const double *h_steps,
                                    int m, double h_target, int stride, int nquad, double *loss, double *grad_h,
                                    double *grad_scale) {
     if (ed == nullptr || h_steps == nullptr || loss == nullptr) return OSMPS_EINVAL;
@@ -1270,7 +1270,7 @@ osmps_status osmps_ed_adjoint_grad(osmps_ed_t *ed, const void *psi0, int nsteps,
 // ---------------------------------------------------------------------------
 // Two-site gates and Trotter evolution (see include/osmps_ed.h)
 // ---------------------------------------------------------------------------
-osmps_status osmps_ed_apply_gates(osmps_ed_t *ed, void *psi, int ngates, const int *site, const double *U) {
+static osmps_status apply_gates_impl(osmps_ed_t *ed, void *psi, int ngates, const int *site, const double *U) {
     if (ed == nullptr || ngates < 0 || (ngates > 0 && (site == nullptr || U == nullptr))) return OSMPS_EINVAL;
     Handle *h = &ed->h;
     CKS(check_state_ptr(h, psi));
@@ -1291,7 +1291,7 @@ osmps_status osmps_ed_apply_gates(osmps_ed_t *ed, void *psi, int ngates, const i
     return OSMPS_OK;
 }
 
-osmps_status osmps_ed_trotter_evolve(osmps_ed_t *ed, void *psi, double dt, int nsteps, int order) {
+static osmps_status trotter_evolve_impl(osmps_ed_t *ed, void *psi, double dt, int nsteps, int order) {
     if (ed == nullptr) return OSMPS_EINVAL;
     Handle *h = &ed->h;
     CKS(check_state_ptr(h, psi));
@@ -1326,7 +1326,7 @@ osmps_status osmps_ed_trotter_evolve(osmps_ed_t *ed, void *psi, double dt, int n
 // ---------------------------------------------------------------------------
 // Reduced density matrices of all pairs and the bond-entropy sweep
 // ---------------------------------------------------------------------------
-osmps_status osmps_ed_rdm_pairs(osmps_ed_t *ed, const void *psi, double *rdm2, double *rdm1) {
+static osmps_status rdm_pairs_impl(osmps_ed_t *ed, const void *psi, double *rdm2, double *rdm1) {
     if (ed == nullptr) return OSMPS_EINVAL;
     Handle *h = &ed->h;
     CKS(check_state_ptr(h, psi));
@@ -1391,6 +1391,42 @@ osmps_status osmps_ed_entropy_sweep(osmps_ed_t *ed, const void *psi, double *S) 
     if (ed->h.L < 2) return OSMPS_EINVAL;
     for (int cut = 1; cut < ed->h.L; ++cut) CKS(osmps_ed_schmidt_entropy(ed, psi, cut, nullptr, &S[cut - 1]));
     return OSMPS_OK;
+}
+
+// Host-side allocations of these calls (small vectors sized by the arguments)
+// must not throw across the C boundary.
+osmps_status osmps_ed_adjoint_grad(osmps_ed_t *ed, const void *psi0, int nsteps, double dt, const double *h_steps,
+                                   int m, double h_target, int stride, int nquad, double *loss, double *grad_h,
+                                   double *grad_scale) {
+    try {
+        return adjoint_grad_impl(ed, psi0, nsteps, dt, h_steps, m, h_target, stride, nquad, loss, grad_h, grad_scale);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
+}
+
+osmps_status osmps_ed_apply_gates(osmps_ed_t *ed, void *psi, int ngates, const int *site, const double *U) {
+    try {
+        return apply_gates_impl(ed, psi, ngates, site, U);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
+}
+
+osmps_status osmps_ed_trotter_evolve(osmps_ed_t *ed, void *psi, double dt, int nsteps, int order) {
+    try {
+        return trotter_evolve_impl(ed, psi, dt, nsteps, order);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
+}
+
+osmps_status osmps_ed_rdm_pairs(osmps_ed_t *ed, const void *psi, double *rdm2, double *rdm1) {
+    try {
+        return rdm_pairs_impl(ed, psi, rdm2, rdm1);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
 }
 
 }  // extern "C"

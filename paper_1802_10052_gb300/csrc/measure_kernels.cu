@@ -631,7 +631,12 @@ osmps_status schmidt_eig_on(Handle *h, cudaStream_t stream, void *solver, void *
     const size_t o_trd = o_copy + ((copy_bytes + 255) & ~(size_t)255);
     const size_t trd_bytes = G > 0 ? trd_workspace_bytes(n, h->prec, G) : 0;
     CKS_(grow_ws(h, ws_p, ws_bytes_p, tracked, o_trd + trd_bytes + 64));
-    std::vector<char> host_ws(host_bytes > 0 ? host_bytes : 1);
+    std::vector<char> host_ws;
+    try {
+        host_ws.resize(host_bytes > 0 ? host_bytes : 1);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
     char *ws = (char *)*ws_p;
     int *info = (int *)ws;
     int *flag = info + 1;

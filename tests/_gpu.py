@@ -2,7 +2,7 @@
 import numpy as np
 import torch
 
-TOL = {"fp64": 1e-10, "mixed": 1e-5}       # relative tolerances of the benchmark spec
+TOL = {"fp64": 1e-10, "mixed": 1e-5}       # relative tolerances of the FP64 and mixed forms
 NP_DT = {"fp64": np.complex128, "mixed": np.complex64}
 
 
