@@ -91,8 +91,8 @@ cudaError_t capture(BatchHandle *b, void *psi, double tol, double *energy, doubl
 
 extern "C" {
 
-osmps_status osmps_ed_batch_create(int n, const int *L, const double *J, const double *alpha, const double *h,
-                                   int prec, int max_iter, void *cuda_stream, osmps_ed_batch_t **out) {
+static osmps_status batch_create_impl(int n, const int *L, const double *J, const double *alpha, const double *h,
+                                      int prec, int max_iter, void *cuda_stream, osmps_ed_batch_t **out) {
     if (out == nullptr) return OSMPS_EINVAL;
     *out = nullptr;
     if (n < 1 || n > (1 << 24) || L == nullptr || J == nullptr || alpha == nullptr || h == nullptr)
@@ -252,7 +252,7 @@ osmps_status osmps_ed_batch_get_split(const osmps_ed_batch_t *ob, int *csize, in
     return OSMPS_OK;
 }
 
-osmps_status osmps_ed_batch_autotune(osmps_ed_batch_t *ob, void *psi, double tol, double *best_ms) {
+static osmps_status batch_autotune_impl(osmps_ed_batch_t *ob, void *psi, double tol, double *best_ms) {
     if (ob == nullptr || psi == nullptr || !(tol >= 0.0) || !std::isfinite(tol)) return OSMPS_EINVAL;
     if ((reinterpret_cast<uintptr_t>(psi) & 15u) != 0) return OSMPS_EINVAL;
     BatchHandle *b = &ob->b;
@@ -351,6 +351,25 @@ osmps_status osmps_ed_batch_launch_count(const osmps_ed_batch_t *ob, int64_t *co
     if (ob == nullptr || count == nullptr) return OSMPS_EINVAL;
     *count = (int64_t)ob->b.launches;
     return OSMPS_OK;
+}
+
+// Host-side allocations of these calls (vectors sized by the arguments) must
+// not throw across the C boundary.
+osmps_status osmps_ed_batch_create(int n, const int *L, const double *J, const double *alpha, const double *h,
+                                   int prec, int max_iter, void *cuda_stream, osmps_ed_batch_t **out) {
+    try {
+        return batch_create_impl(n, L, J, alpha, h, prec, max_iter, cuda_stream, out);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
+}
+
+osmps_status osmps_ed_batch_autotune(osmps_ed_batch_t *ob, void *psi, double tol, double *best_ms) {
+    try {
+        return batch_autotune_impl(ob, psi, tol, best_ms);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
 }
 
 }  // extern "C"
