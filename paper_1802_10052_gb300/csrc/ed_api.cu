@@ -1389,7 +1389,12 @@ static osmps_status rdm_pairs_impl(osmps_ed_t *ed, const void *psi, double *rdm2
 osmps_status osmps_ed_entropy_sweep(osmps_ed_t *ed, const void *psi, double *S) {
     if (ed == nullptr || S == nullptr) return OSMPS_EINVAL;
     if (ed->h.L < 2) return OSMPS_EINVAL;
-    for (int cut = 1; cut < ed->h.L; ++cut) CKS(osmps_ed_schmidt_entropy(ed, psi, cut, nullptr, &S[cut - 1]));
+    // largest blocks first, so the Gram and solver workspaces are sized once
+    const int L = ed->h.L;
+    for (int ls = L / 2; ls >= 1; --ls) {
+        CKS(osmps_ed_schmidt_entropy(ed, psi, ls, nullptr, &S[ls - 1]));
+        if (L - ls != ls) CKS(osmps_ed_schmidt_entropy(ed, psi, L - ls, nullptr, &S[L - ls - 1]));
+    }
     return OSMPS_OK;
 }
 
