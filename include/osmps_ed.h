@@ -121,6 +121,17 @@ osmps_status osmps_ed_set_gram_mode(osmps_ed_t *ed, int mode);
  * (scheduling). */
 osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm);
 
+/* How osmps_ed_schmidt_entropy obtains the Schmidt values (Sec. IV bond
+ * entropy).  0 (default): Gram product rho_A = M M^dag (tensor cores for
+ * complex64) and a Hermitian eigen-solve; every Schmidt value then carries
+ * an absolute error of order the working precision, which dominates S of
+ * weakly entangled complex64 states.  1: squared singular values of the
+ * block matrix M itself (library SVD, no Gram product): tiny Schmidt values
+ * keep their accuracy (S within ~1e-10 in complex64) at several times the
+ * cost.  Method 1 is not available to osmps_ed_schmidt_entropy_async
+ * (EUNSUPPORTED).  Not from the paper (numerics). */
+osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);
+
 /* L2 prefetch distance of the H.psi passes: each CTA asks L2 (TMA prefetch)
  * for the tiles it will stage `tiles` steps after the ones its shared-memory
  * stages hold; 0 = off.  Default 1 for OSMPS_MIXED, 0 for OSMPS_FP64.

@@ -265,6 +265,11 @@ class Chain:
         """Size the handle's grids for nsm SMs (0: all of the device)."""
         check(lib.osmps_ed_set_sm_count(self._h, int(nsm)), "osmps_ed_set_sm_count")
 
+    def set_entropy_method(self, method):
+        """0: Gram product + Hermitian eigen-solve (fast); 1: singular values of M
+        (accurate small Schmidt values in complex64, slower)."""
+        check(lib.osmps_ed_set_entropy_method(self._h, int(method)), "osmps_ed_set_entropy_method")
+
     def set_prefetch(self, tiles):
         """L2 prefetch distance of the H.psi passes (tiles ahead; 0 = off)."""
         check(lib.osmps_ed_set_prefetch(self._h, int(tiles)), "osmps_ed_set_prefetch")

@@ -753,6 +753,12 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm) {
     return OSMPS_OK;
 }
 
+osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method) {
+    if (ed == nullptr || (method != 0 && method != 1)) return OSMPS_EINVAL;
+    ed->h.entropy_method = method;
+    return OSMPS_OK;
+}
+
 osmps_status osmps_ed_set_prefetch(osmps_ed_t *ed, int tiles) {
     if (ed == nullptr || tiles < 0 || tiles > 4) return OSMPS_EINVAL;
     ed->h.prefetch = tiles;
@@ -977,6 +983,25 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
     const int ls = cut < L - cut ? cut : L - cut;
     const int n = 1 << ls;
     const size_t gbytes = (size_t)n * n * h->esize;
+    if (h->entropy_method == 1) {
+        // singular values of M: no Gram product
+        if ((size_t)n + 1 > h->lam_cap) {
+            dev_free(h, h->lam_dev, h->lam_cap * sizeof(double));
+            h->lam_dev = nullptr;
+            h->lam_cap = 0;
+            cudaError_t err;
+            h->lam_dev = (double *)dev_alloc(h, sizeof(double) * (n + 1), &err);
+            if (err != cudaSuccess) return from_cuda(err);
+            h->lam_cap = n + 1;
+        }
+        CKS(schmidt_svd(h, psi, cut, h->lam_dev, h->lam_dev + n));
+        if (lambda) CK(cudaMemcpyAsync(lambda, h->lam_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+        double Sv = 0.0;
+        CK(cudaMemcpyAsync(&Sv, h->lam_dev + n, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (S) *S = Sv;
+        return OSMPS_OK;
+    }
     if (gbytes > h->gram_bytes) {
         dev_free(h, h->gram, h->gram_bytes);
         h->gram = nullptr;
@@ -1022,6 +1047,7 @@ osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int
     if (L < 2 || cut < 1 || cut > L - 1) return OSMPS_EINVAL;
     const int ls = cut < L - cut ? cut : L - cut;
     const int n = 1 << ls;
+    if (h->entropy_method != 0) return OSMPS_EUNSUPPORTED;  // the asynchronous call takes the Gram route
     if (ed->am == nullptr) CKS(create_async(h, &ed->am));
     AsyncMeas *am = ed->am;
     if (am->own_G > 0) return entropy_async_own(h, am, psi, cut, n, S, lambda);

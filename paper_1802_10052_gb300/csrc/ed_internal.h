@@ -116,6 +116,9 @@ cudaError_t launch_gram(Handle *h, const void *psi, int cut, void *rho, int *n_o
 bool gram_tc_supported(int n, long long K);
 cudaError_t gram_tc_launch(Handle *h, const void *psi, int n, long long K, void *rho, float *planes, float *G);
 osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev);
+// Schmidt values of the cut as squared singular values of the block matrix M of psi
+// (no Gram product); lambda_dev: 2^min(cut, L-cut) values, descending, then S
+osmps_status schmidt_svd(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev);
 // S and the descending spectrum from ascending FP64 eigenvalues w (n values) on a stream
 cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *lambda_dev, double *S_dev);
 
@@ -183,6 +186,7 @@ struct Handle {
     size_t gram_aux_bytes;
     int gram_mode;              // 0 automatic, 1 CUDA cores, 2 tensor cores
     int prefetch;               // L2 prefetch distance of the H.psi passes (tiles)
+    int entropy_method;         // 0: Gram product + Hermitian eigen-solve, 1: singular values of M
     void *solver_ws;            // cuSOLVER workspace
     size_t solver_ws_bytes;
     double *lam_dev;

@@ -474,6 +474,8 @@ struct SolverLib {
     decltype(&cusolverDnCreateParams) create_params = nullptr;
     decltype(&cusolverDnXsyevd_bufferSize) x_bufsize = nullptr;
     decltype(&cusolverDnXsyevd) x_eig = nullptr;
+    decltype(&cusolverDnXgesvd_bufferSize) x_svd_bufsize = nullptr;
+    decltype(&cusolverDnXgesvd) x_svd = nullptr;
     cusolverDnParams_t params = nullptr;  // default options, read-only after creation
 };
 static SolverLib g_solver;
@@ -501,6 +503,8 @@ static bool load_solver() {
     g_solver.create_params = (decltype(g_solver.create_params))dlsym(g_solver.so, "cusolverDnCreateParams");
     g_solver.x_bufsize = (decltype(g_solver.x_bufsize))dlsym(g_solver.so, "cusolverDnXsyevd_bufferSize");
     g_solver.x_eig = (decltype(g_solver.x_eig))dlsym(g_solver.so, "cusolverDnXsyevd");
+    g_solver.x_svd_bufsize = (decltype(g_solver.x_svd_bufsize))dlsym(g_solver.so, "cusolverDnXgesvd_bufferSize");
+    g_solver.x_svd = (decltype(g_solver.x_svd))dlsym(g_solver.so, "cusolverDnXgesvd");
     if (!g_solver.create_params || !g_solver.x_bufsize || !g_solver.x_eig ||
         g_solver.create_params(&g_solver.params) != CUSOLVER_STATUS_SUCCESS)
         g_solver.params = nullptr;
@@ -694,6 +698,121 @@ cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *
 osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double *S_dev) {
     return schmidt_eig_on(h, h->stream, nullptr, &h->solver_ws, &h->solver_ws_bytes, true, &h->launches, rho, n,
                           lambda_dev, S_dev);
+}
+
+// ---------------------------------------------------------------------------
+// Schmidt values from the singular values of M itself (no Gram product):
+// lambda = sigma^2 keeps an absolute error of ~2 sigma eps, so tiny Schmidt
+// values stay accurate in complex64, where forming rho = M M^H would give
+// every lambda an error of ~eps.
+// ---------------------------------------------------------------------------
+
+// A[a + c*m] = psi[a*nc + c]: the row-major m x nc block matrix, column-major
+template <typename C>
+__global__ void transpose_kernel(const C *psi, long long m, long long nc, C *A) {
+    __shared__ C t[32][33];
+    const long long a0 = (long long)blockIdx.x * 32, c0 = (long long)blockIdx.y * 32;  // rows on x (up to 2^29)
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long a = a0 + r, c = c0 + threadIdx.x;
+        if (a < m && c < nc) t[r][threadIdx.x] = psi[a * nc + c];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long c = c0 + r, a = a0 + threadIdx.x;
+        if (a < m && c < nc) A[a + c * m] = t[threadIdx.x][r];
+    }
+}
+
+// lambda_i = sigma_i^2 (descending as returned), S = -sum lambda ln lambda;
+// flag = 1 on a reported failure or a non-finite value
+template <typename T>
+__global__ void sv_entropy_kernel(const T *sv, int n, const int *info, double *lambda, double *S, int *flag) {
+    __shared__ double red[32];
+    double s = 0.0;
+    int bad = (threadIdx.x == 0 && *info != 0) ? 1 : 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = (double)sv[i];
+        if (!isfinite(x)) bad = 1;
+        const double l = x * x;
+        lambda[i] = l;
+        if (l > 0.0) s -= l * log(l);
+    }
+    bad = __syncthreads_or(bad);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        *S = t;
+        *flag = bad;
+    }
+}
+
+osmps_status schmidt_svd(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev) {
+    std::lock_guard<std::mutex> lock(g_solver_mu);
+    if (!load_solver() || g_solver.params == nullptr || !g_solver.x_svd || !g_solver.x_svd_bufsize)
+        return OSMPS_EUNSUPPORTED;
+    if (g_solver.set_stream(g_solver.handle, h->stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+    const int L = h->L;
+    const bool dbl = (h->prec == OSMPS_FP64);
+    // column-major m x nc with m >= nc
+    const bool left_small = cut <= L - cut;
+    const long long m = 1ll << (left_small ? L - cut : cut), nc = 1ll << (left_small ? cut : L - cut);
+    const cudaDataType ta = dbl ? CUDA_C_64F : CUDA_C_32F, tr = dbl ? CUDA_R_64F : CUDA_R_32F;
+    const size_t cs = h->esize, rs = dbl ? sizeof(double) : sizeof(float);
+    const size_t abytes = (size_t)m * (size_t)nc * cs;
+    // layout: info, flag | singular values | U, VT (not referenced: jobu = jobvt = 'N') | A | work
+    const size_t o_s = 256, o_u = o_s + ((nc * rs + 255) & ~(size_t)255), o_vt = o_u + 256, o_a = o_vt + 256;
+    const size_t o_work = o_a + ((abytes + 255) & ~(size_t)255);
+    CKS_(grow_ws(h, &h->solver_ws, &h->solver_ws_bytes, true, o_work + 256));
+    size_t work_bytes = 0, host_bytes = 0;
+    {
+        char *ws = (char *)h->solver_ws;
+        if (g_solver.x_svd_bufsize(g_solver.handle, g_solver.params, 'N', 'N', m, nc, ta, ws + o_a, m, tr, ws + o_s, ta,
+                                   ws + o_u, m, ta, ws + o_vt, nc, ta, &work_bytes, &host_bytes) !=
+            CUSOLVER_STATUS_SUCCESS)
+            return OSMPS_ECUDA;
+    }
+    if (work_bytes < 256) work_bytes = 256;
+    CKS_(grow_ws(h, &h->solver_ws, &h->solver_ws_bytes, true, o_work + work_bytes + 64));
+    std::vector<char> host_ws;
+    try {
+        host_ws.resize(host_bytes > 0 ? host_bytes : 1);
+    } catch (...) {
+        return OSMPS_ENOMEM;
+    }
+    char *ws = (char *)h->solver_ws;
+    int *info = (int *)ws, *flag = info + 1;
+    if (left_small) {
+        // the row-major block matrix read column-major is already m x nc with lda = m
+        if (cudaMemcpyAsync(ws + o_a, psi, abytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            return OSMPS_ECUDA;
+    } else {
+        const dim3 grid((unsigned)((m + 31) / 32), (unsigned)((nc + 31) / 32)), block(32, 8);
+        if (dbl)
+            transpose_kernel<double2><<<grid, block, 0, h->stream>>>((const double2 *)psi, m, nc, (double2 *)(ws + o_a));
+        else
+            transpose_kernel<float2><<<grid, block, 0, h->stream>>>((const float2 *)psi, m, nc, (float2 *)(ws + o_a));
+        h->launches += 1;
+    }
+    if (g_solver.x_svd(g_solver.handle, g_solver.params, 'N', 'N', m, nc, ta, ws + o_a, m, tr, ws + o_s, ta, ws + o_u,
+                       m, ta, ws + o_vt, nc, ta, ws + o_work, work_bytes, host_ws.data(), host_bytes, info) !=
+        CUSOLVER_STATUS_SUCCESS)
+        return OSMPS_ECUDA;
+    if (dbl)
+        sv_entropy_kernel<double><<<1, 1024, 0, h->stream>>>((const double *)(ws + o_s), (int)nc, info, lambda_dev,
+                                                             S_dev, flag);
+    else
+        sv_entropy_kernel<float><<<1, 1024, 0, h->stream>>>((const float *)(ws + o_s), (int)nc, info, lambda_dev,
+                                                            S_dev, flag);
+    h->launches += 1;
+    int bad = 0;
+    if (cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return OSMPS_ECUDA;
+    return bad == 0 ? OSMPS_OK : OSMPS_ECUDA;
 }
 
 }  // namespace osmps
