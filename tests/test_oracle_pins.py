@@ -90,6 +90,28 @@ def test_diagonal_closed_forms():
     assert abs(neel(30, 1.0) - (-20.302744130741935)) < 1e-12
 
 
+def test_coupling_table_by_hand():
+    # J(r) = J / r^alpha typed out by hand (index r-1): 2^-1.5 = 1/(2 sqrt 2),
+    # 3^-1.5 = 1/(3 sqrt 3), 4^-1.5 = 1/8; an off-by-one in r or a dropped J fails here
+    np.testing.assert_allclose(O.coupling_table(5, 1.0, 1.5),
+                               [1.0, 0.35355339059327373, 0.19245008972987526, 0.125], rtol=1e-15, atol=0)
+    np.testing.assert_allclose(O.coupling_table(4, -1.3, 2.0), [-1.3, -0.325, -0.14444444444444443],
+                               rtol=1e-15, atol=0)
+    np.testing.assert_array_equal(O.coupling_table(4, 0.6, 0.0), [0.6, 0.6, 0.6])
+    # nearest neighbours only for alpha None or +inf; the table argument overrides both
+    np.testing.assert_array_equal(O.coupling_table(4, 2.0, None), [2.0, 0.0, 0.0])
+    np.testing.assert_array_equal(O.coupling_table(4, 2.0, math.inf), [2.0, 0.0, 0.0])
+    np.testing.assert_array_equal(O.coupling_table(3, 1.0, 1.5, table=[0.1, -0.2]), [0.1, -0.2])
+    assert O.coupling_table(1, 1.0, 1.5).shape == (0,)
+    # the all-up diagonal energy sum_r (L - r) J(r) of the L = 24, alpha = 1.5 quench,
+    # through coupling_table and through the oracle's pair loop, against the typed value
+    Jr = O.coupling_table(24, 1.0, 1.5)
+    assert abs(sum((24 - r) * Jr[r - 1] for r in range(1, 24)) - 44.560736401070486) < 1e-12
+    assert abs(O.diagonal_energy(24, Jr, np.array([0]))[0] - 44.560736401070486) < 1e-12
+    Jr = O.coupling_table(30, 1.0, 1.0)
+    assert abs(O.diagonal_energy(30, Jr, np.array([si.neel_index(30)]))[0] - (-20.302744130741935)) < 1e-12
+
+
 # --------------------------------------------------------------------------
 # Ground state
 # --------------------------------------------------------------------------
