@@ -122,14 +122,30 @@ osmps_status osmps_ed_set_gram_mode(osmps_ed_t *ed, int mode);
 osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm);
 
 /* How osmps_ed_schmidt_entropy obtains the Schmidt values (Sec. IV bond
- * entropy).  0 (default): Gram product rho_A = M M^dag (tensor cores for
- * complex64) and a Hermitian eigen-solve; every Schmidt value then carries
- * an absolute error of order the working precision, which dominates S of
- * weakly entangled complex64 states.  1: squared singular values of the
- * block matrix M itself (library SVD, no Gram product): tiny Schmidt values
- * keep their accuracy (S within ~1e-10 in complex64) at several times the
- * cost.  Method 1 is not available to osmps_ed_schmidt_entropy_async
- * (EUNSUPPORTED).  Not from the paper (numerics). */
+ * entropy).  Not from the paper (numerics).
+ *   0  Gram product rho_A = M M^dag (tensor cores for complex64) and its
+ *      eigenvalues.  Every Schmidt value then carries an absolute error of
+ *      order the working precision; in complex64 that noise reaches ~2e-5 in S
+ *      of a weakly entangled L = 24 state.
+ *   1  squared singular values of the block matrix M itself (library SVD on a
+ *      copy of M, no Gram product): accurate (~2e-7 in S in complex64) at ~5x
+ *      the cost of 0.  The copy (2^L amplitudes) and the library workspace stay
+ *      with the handle after the call and are counted by osmps_ed_device_bytes;
+ *      ENOMEM when they do not fit.
+ *   2  Rayleigh quotients (complex64 only; 128 <= 2^min(cut, L-cut) <= 8192):
+ *      the eigenvectors u_i of the Gram product (library solver), then
+ *      Lambda_i = |u_i^dag M|^2 from M itself on the tensor cores, all
+ *      rescaled to sum to <psi|psi> (FP64).  No value is formed by squaring M
+ *      in FP32, so S keeps ~1e-7 in complex64 at ~1.1x the cost of 0; values
+ *      of nearly equal size (closer than ~1e-7) come out as averages of each
+ *      other, which moves S only at second order.  Scratch (4 n^2 + 2 n K complex-sized floats) is kept by the handle.
+ *      Falls back to 1 when the library eigen-solver fails.  EUNSUPPORTED
+ *      where it does not apply.
+ *   3  automatic (the default): complex128 takes 0 (FP64 Gram and eigenvalues
+ *      meet 1e-10); complex64 takes 2 where it applies, else 1 for blocks up
+ *      to 8192 rows, else 0.
+ * osmps_ed_schmidt_entropy_async takes method 0 (also when 3 is set) and
+ * returns EUNSUPPORTED for 1 and 2. */
 osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);
 
 /* L2 prefetch distance of the H.psi passes: each CTA asks L2 (TMA prefetch)
@@ -276,9 +292,11 @@ osmps_status osmps_ed_measure_zz_noalloc(int L, int prec, const void *psi, doubl
  *   cut      1 <= cut <= L-1, or -1 for floor(L/2).
  *   lambda   host array of 2^min(cut, L-cut) doubles (descending), or NULL.
  *   S        host output (may be NULL); eigenvalues <= 0 contribute 0.
- * The Gram product runs on this library's kernels; the Hermitian eigenvalue
- * problem is solved by cuSOLVER (heevd), loaded at first use.  Returns
- * EUNSUPPORTED if cuSOLVER cannot be loaded.  Synchronises.
+ * How the Schmidt values are obtained is set by osmps_ed_set_entropy_method
+ * (default: the most accurate route that applies).  The products run on this
+ * library's kernels; the Hermitian eigen-solve and the SVD are cuSOLVER's,
+ * loaded at first use.  Returns EUNSUPPORTED if cuSOLVER cannot be loaded.
+ * Synchronises.
  */
 osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, double *lambda,
                                       double *S);
@@ -323,6 +341,19 @@ osmps_status osmps_ed_set_async_eigensolver(osmps_ed_t *ed, int ctas);
  * written its results; returns the first error among them (then clears it).
  * Call it before osmps_ed_destroy when measurements are outstanding. */
 osmps_status osmps_ed_measure_wait(osmps_ed_t *ed);
+
+/*
+ * Check of the failure path of the bounded device waits (not from the paper;
+ * failure detection).  Enqueues one kernel that waits, with the same bounded
+ * mbarrier wait the H.psi and Gram kernels use, for a barrier phase that
+ * nothing completes (complete = 0) or that the kernel completes itself first
+ * (complete = 1).  The wait gives up after `seconds` (0 < seconds <= 2; the
+ * library's own kernels give up after 2 s), raises the handle's error word and
+ * returns; the next synchronising call of the handle (energy, Lanczos, Krylov)
+ * then returns OSMPS_ETIMEOUT and clears the word, and the handle stays usable.
+ * No fault, trap or hang is involved.  Enqueues only.
+ */
+osmps_status osmps_ed_probe_wait(osmps_ed_t *ed, double seconds, int complete);
 
 /*
  * Timing of the H.psi products with CUDA events recorded on the handle's

@@ -266,8 +266,8 @@ class Chain:
         check(lib.osmps_ed_set_sm_count(self._h, int(nsm)), "osmps_ed_set_sm_count")
 
     def set_entropy_method(self, method):
-        """0: Gram product + Hermitian eigen-solve (fast); 1: singular values of M
-        (accurate small Schmidt values in complex64, slower)."""
+        """0: eigenvalues of the Gram product; 1: singular values of M; 2: Rayleigh
+        quotients of the Gram product's eigenvectors (complex64); 3: automatic (default)."""
         check(lib.osmps_ed_set_entropy_method(self._h, int(method)), "osmps_ed_set_entropy_method")
 
     def set_prefetch(self, tiles):

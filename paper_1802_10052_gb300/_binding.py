@@ -56,6 +56,7 @@ SIGNATURES = {
     "osmps_ed_set_prefetch": (_I, [_P, _I]),
     "osmps_ed_set_entropy_method": (_I, [_P, _I]),
     "osmps_ed_launch_count": (_I, [_P, C.POINTER(C.c_int64)]),
+    "osmps_ed_probe_wait": (_I, [_P, _D, _I]),
     "osmps_ed_timing_enable": (_I, [_P, _I]),
     "osmps_ed_timing_read": (_I, [_P, _DP, C.POINTER(C.c_int64), _I]),
     "osmps_ed_batch_create": (_I, [_I, C.POINTER(_I), _DP, _DP, _DP, _I, _I, _P, C.POINTER(_P)]),

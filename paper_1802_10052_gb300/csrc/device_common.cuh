@@ -96,17 +96,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Wait for the phase of the given parity.  try_wait itself suspends the
 // thread for a while; the timer (and the error flag raised by another warp)
 // is consulted only every 64 polls, so a completed phase is seen at once.
-// Gives up after kWaitNs.
-static __device__ __noinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, const int *err) {
+// Gives up after limit_ns (kWaitNs for the kernels of this library).
+static __device__ __noinline__ bool mbar_wait_ns(unsigned long long *bar, unsigned parity, const int *err,
+                                                 unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*(volatile const int *)err != 0) return false;
-            if (global_ns() - t0 > kWaitNs) return false;
+            if (global_ns() - t0 > limit_ns) return false;
         }
     }
+}
+static __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, const int *err) {
+    return mbar_wait_ns(bar, parity, err, kWaitNs);
 }
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(

@@ -15,6 +15,7 @@
 #include <thread>
 #include <vector>
 
+#include "device_common.cuh"
 #include "ed_internal.h"
 
 using namespace osmps;
@@ -178,6 +179,20 @@ osmps_status sync_and_check(Handle *h) {
         return OSMPS_ETIMEOUT;
     }
     return OSMPS_OK;
+}
+
+// One thread waits, with the bounded wait of the H.psi and Gram kernels, for
+// the first phase of an mbarrier that nothing arrives at (complete = 0), or
+// that it completed itself (complete = 1); raises the error word when the
+// wait gives up.
+__global__ void probe_wait_kernel(KrylovCtl *ctl, unsigned long long limit_ns, int complete) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (complete) mbar_arrive(&bar);
+    if (!mbar_wait_ns(&bar, 0u, &ctl->error, limit_ns)) atomicExch(&ctl->error, 1);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
 }
 
 __global__ void ctl_init_kernel(KrylovCtl *ctl, double bd_tol) {
@@ -593,6 +608,15 @@ osmps_status osmps_ed_launch_count(const osmps_ed_t *ed, int64_t *count) {
     return OSMPS_OK;
 }
 
+osmps_status osmps_ed_probe_wait(osmps_ed_t *ed, double seconds, int complete) {
+    if (ed == nullptr || !(seconds > 0.0) || seconds > 2.0 || (complete != 0 && complete != 1)) return OSMPS_EINVAL;
+    Handle *h = &ed->h;
+    probe_wait_kernel<<<1, 32, 0, h->stream>>>(h->ctl, (unsigned long long)(seconds * 1e9), complete);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    return OSMPS_OK;
+}
+
 osmps_status osmps_ed_timing_enable(osmps_ed_t *ed, int enable) {
     if (ed == nullptr) return OSMPS_EINVAL;
     ed->h.timing = enable ? 1 : 0;
@@ -656,6 +680,7 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
     for (int r = 0; r <= kMaxL; ++r) hd->Jr[r] = Jr[r];
     for (int b = 0; b < L; ++b) hd->hbit[b] = h;
     hd->reorth = 0;
+    hd->entropy_method = ENT_AUTO;
     hd->prefetch = (prec == OSMPS_FP64) ? 0 : 1;  // FP64 passes are bound by the FP64 pipe, not by latency
     cudaError_t err = cudaGetDevice(&hd->device);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&hd->nsm, cudaDevAttrMultiProcessorCount, hd->device);
@@ -754,7 +779,7 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm) {
 }
 
 osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method) {
-    if (ed == nullptr || (method != 0 && method != 1)) return OSMPS_EINVAL;
+    if (ed == nullptr || method < ENT_GRAM || method > ENT_AUTO) return OSMPS_EINVAL;
     ed->h.entropy_method = method;
     return OSMPS_OK;
 }
@@ -983,7 +1008,49 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
     const int ls = cut < L - cut ? cut : L - cut;
     const int n = 1 << ls;
     const size_t gbytes = (size_t)n * n * h->esize;
-    if (h->entropy_method == 1) {
+    int method = h->entropy_method;
+    if (method == ENT_AUTO) {
+        if (h->prec == OSMPS_FP64)
+            method = ENT_GRAM;
+        else
+            method = rayleigh_applicable(h, cut) ? ENT_RAYLEIGH : (n <= 8192 ? ENT_SVD : ENT_GRAM);
+    }
+    if (method == ENT_RAYLEIGH && !rayleigh_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
+    if (method == ENT_RAYLEIGH) {
+        if (gbytes > h->gram_bytes) {
+            dev_free(h, h->gram, h->gram_bytes);
+            h->gram = nullptr;
+            h->gram_bytes = 0;
+            cudaError_t err;
+            h->gram = dev_alloc(h, gbytes, &err);
+            if (err != cudaSuccess) return from_cuda(err);
+            h->gram_bytes = gbytes;
+        }
+        if ((size_t)n + 1 > h->lam_cap) {
+            dev_free(h, h->lam_dev, h->lam_cap * sizeof(double));
+            h->lam_dev = nullptr;
+            h->lam_cap = 0;
+            cudaError_t err;
+            h->lam_dev = (double *)dev_alloc(h, sizeof(double) * (n + 1), &err);
+            if (err != cudaSuccess) return from_cuda(err);
+            h->lam_cap = n + 1;
+        }
+        const osmps_status rs = schmidt_rayleigh(h, psi, cut, h->gram, h->lam_dev, h->lam_dev + n);
+        if (rs == OSMPS_ENOCONV)
+            method = ENT_SVD;  // the library eigen-solver failed: singular values of M instead
+        else if (rs != OSMPS_OK)
+            return rs;
+        else {
+            if (lambda)
+                CK(cudaMemcpyAsync(lambda, h->lam_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+            double Sv = 0.0;
+            CK(cudaMemcpyAsync(&Sv, h->lam_dev + n, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            if (S) *S = Sv;
+            return OSMPS_OK;
+        }
+    }
+    if (method == ENT_SVD) {
         // singular values of M: no Gram product
         if ((size_t)n + 1 > h->lam_cap) {
             dev_free(h, h->lam_dev, h->lam_cap * sizeof(double));
@@ -1047,7 +1114,8 @@ osmps_status osmps_ed_schmidt_entropy_async(osmps_ed_t *ed, const void *psi, int
     if (L < 2 || cut < 1 || cut > L - 1) return OSMPS_EINVAL;
     const int ls = cut < L - cut ? cut : L - cut;
     const int n = 1 << ls;
-    if (h->entropy_method != 0) return OSMPS_EUNSUPPORTED;  // the asynchronous call takes the Gram route
+    // the asynchronous call takes the Gram route (the automatic choice included)
+    if (h->entropy_method != ENT_GRAM && h->entropy_method != ENT_AUTO) return OSMPS_EUNSUPPORTED;
     if (ed->am == nullptr) CKS(create_async(h, &ed->am));
     AsyncMeas *am = ed->am;
     if (am->own_G > 0) return entropy_async_own(h, am, psi, cut, n, S, lambda);
@@ -1154,14 +1222,17 @@ static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nste
         ls = alloc(vb);
         w1 = alloc(vb);
         w0 = alloc(vb);
-        zd = static_cast<double *>(alloc(sizeof(double) * 4 * 32));
+        // <ls|X ps> and <ls|H_zz ps> of every node of every step, read back once at the end
+        zd = static_cast<double *>(alloc(sizeof(double) * 4 * (size_t)nquad * nsteps));
     }
     osmps_ed_t *sib = nullptr;  // second handle: Krylov basis of the adjoint state
+    osmps_ed_t *xop = nullptr;  // third handle: X = sum_k sigma^x_k alone (no couplings, unit field)
     auto cleanup = [&]() {
         cudaStreamSynchronize(h->stream);
         for (void *p : bufs)
             if (p != nullptr) cudaFree(p);
         if (sib != nullptr) osmps_ed_destroy(sib);
+        if (xop != nullptr) osmps_ed_destroy(xop);
         std::memcpy(h->hbit, hb_save, sizeof(hb_save));
     };
     auto fail = [&](osmps_status e) {
@@ -1213,6 +1284,9 @@ static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nste
         for (int r = 1; r < h->L; ++r) Jr1[r - 1] = h->Jr[r];
         CKA(osmps_ed_create(h->L, h->L > 1 ? Jr1 : nullptr, 0.0, -1.0, 0.0, h->prec, h->stream, &sib));
         sib->h.reorth = h->reorth;
+        double J0[kMaxL] = {0.0};
+        CKA(osmps_ed_create(h->L, h->L > 1 ? J0 : nullptr, 0.0, -1.0, 1.0, h->prec, h->stream, &xop));
+        xop->h.nsm = h->nsm;
     }
     Handle *hb = &sib->h;
     std::vector<double> xs(nquad), ws(nquad), gh(nsteps, 0.0);
@@ -1230,7 +1304,7 @@ static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nste
         a.epilogue = EPI_PLAIN;
         CKAC(launch_hpsi(h, a, &np));
     }
-    std::vector<double> zh(4 * nquad);
+    std::vector<double> zh(4 * (size_t)nquad * nsteps);
     const int nseg = (nsteps + stride - 1) / stride;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int k0 = sgi * stride, k1 = std::min(nsteps, k0 + stride);
@@ -1250,40 +1324,45 @@ static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nste
             CKA(krylov_basis(hb, lam, m));
             // Frechet derivative of exp(-i dt H) along X and along H_zz, by Gauss-Legendre in s:
             //   <lambda_k| L(A, E) psi_{k-1}> = int_0^1 <e^{i s dt H} lambda_k| E |e^{-i (1-s) dt H} psi_{k-1}> ds
+            double *zk = zd + 4 * (size_t)nquad * (k - 1);
             for (int q = 0; q < nquad; ++q) {
                 CKA(krylov_combine(h, m, (1.0 - xs[q]) * dt, ps));
                 CKA(krylov_combine(hb, m, -xs[q] * dt, ls));
                 int np = 0;
                 HpsiArgs a{};
                 a.u = ps;
-                a.tmp = h->tmp;
-                a.partials = h->partials;
                 a.epilogue = EPI_PLAIN;
-                set_h(h, 1.0);
+                a.partials = xop->h.partials;
+                a.tmp = xop->h.tmp;
                 a.out = w1;
-                CKAC(launch_hpsi(h, a, &np));  // H_zz ps + X ps
+                CKAC(launch_hpsi(&xop->h, a, &np));  // X ps
                 set_h(h, 0.0);
+                a.partials = h->partials;
+                a.tmp = h->tmp;
                 a.out = w0;
                 CKAC(launch_hpsi(h, a, &np));  // H_zz ps
-                CKAC(launch_cdot(h, ls, w1, zd + 4 * q));
-                CKAC(launch_cdot(h, ls, w0, zd + 4 * q + 2));
+                CKAC(launch_cdot(h, ls, w1, zk + 4 * q));
+                CKAC(launch_cdot(h, ls, w0, zk + 4 * q + 2));
             }
             // lambda_{k-1} = exp(+i dt H(h_k)) lambda_k
             CKA(krylov_combine(hb, m, -dt, lam));
-            CKAC(cudaMemcpyAsync(zh.data(), zd, sizeof(double) * 4 * nquad, cudaMemcpyDeviceToHost, h->stream));
-            CKAC(cudaStreamSynchronize(h->stream));
-            double gk = 0.0;
-            for (int q = 0; q < nquad; ++q) {
-                // d/dh_k: E = -i dt X, 2 Re(-i dt z) = 2 dt Im z with z = <ls| X ps> = z1 - z0
-                gk += ws[q] * 2.0 * dt * (zh[4 * q + 1] - zh[4 * q + 3]);
-                // d/ds: E = -i dt H_zz
-                gs += ws[q] * 2.0 * dt * zh[4 * q + 3];
-            }
-            gh[k - 1] = gk;
         }
     }
+    CKAC(cudaMemcpyAsync(zh.data(), zd, sizeof(double) * zh.size(), cudaMemcpyDeviceToHost, h->stream));
     CKA(sync_and_check(h));
     CKA(sync_and_check(hb));
+    CKA(sync_and_check(&xop->h));
+    for (int k = 1; k <= nsteps; ++k) {
+        const double *zk = zh.data() + 4 * (size_t)nquad * (k - 1);
+        double gk = 0.0;
+        for (int q = 0; q < nquad; ++q) {
+            // d/dh_k: E = -i dt X, 2 Re(-i dt z) = 2 dt Im z with z = <ls| X ps>
+            gk += ws[q] * 2.0 * dt * zk[4 * q + 1];
+            // d/ds: E = -i dt H_zz
+            gs += ws[q] * 2.0 * dt * zk[4 * q + 3];
+        }
+        gh[k - 1] = gk;
+    }
     if (grad_h != nullptr)
         for (int k = 0; k < nsteps; ++k) grad_h[k] = gh[k];
     if (grad_scale != nullptr) *grad_scale = gs;

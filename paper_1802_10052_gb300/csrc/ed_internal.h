@@ -119,6 +119,23 @@ osmps_status schmidt_eig(Handle *h, void *rho, int n, double *lambda_dev, double
 // Schmidt values of the cut as squared singular values of the block matrix M of psi
 // (no Gram product); lambda_dev: 2^min(cut, L-cut) values, descending, then S
 osmps_status schmidt_svd(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev);
+// Schmidt values as Rayleigh quotients |u_i^H A|^2 of the eigenvectors of rho = A A^H
+// (complex64; rescaled to the FP64 norm): rho is the n x n Gram buffer;
+// OSMPS_ENOCONV when the library eigen-solver failed (callers then take schmidt_svd)
+bool rayleigh_applicable(const Handle *h, int cut);
+osmps_status schmidt_rayleigh(Handle *h, const void *psi, int cut, void *rho, double *lambda_dev, double *S_dev);
+bool rayleigh_tc_supported(int n, long long K);
+size_t rayleigh_tc_plane_floats(int n, long long K);
+cudaError_t rayleigh_tc_launch(Handle *h, const void *R, const void *psi, int n, long long K, long long sx,
+                               long long sk, float *planes, double *part_re, double *part_im);
+// how osmps_ed_schmidt_entropy obtains the Schmidt values
+enum EntropyMethod : int {
+    ENT_GRAM = 0,      // eigenvalues of the Gram product
+    ENT_SVD = 1,       // squared singular values of M
+    ENT_RAYLEIGH = 2,  // Rayleigh quotients of the Gram product's eigenvectors (complex64)
+    ENT_AUTO = 3       // complex64: Rayleigh where it applies, else singular values up to 2^13 rows,
+                       // else Gram; complex128: Gram
+};
 // S and the descending spectrum from ascending FP64 eigenvalues w (n values) on a stream
 cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *lambda_dev, double *S_dev);
 
@@ -186,7 +203,7 @@ struct Handle {
     size_t gram_aux_bytes;
     int gram_mode;              // 0 automatic, 1 CUDA cores, 2 tensor cores
     int prefetch;               // L2 prefetch distance of the H.psi passes (tiles)
-    int entropy_method;         // 0: Gram product + Hermitian eigen-solve, 1: singular values of M
+    int entropy_method;         // EntropyMethod
     void *solver_ws;            // cuSOLVER workspace
     size_t solver_ws_bytes;
     double *lam_dev;

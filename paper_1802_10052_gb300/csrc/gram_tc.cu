@@ -16,12 +16,18 @@
 //           and add it into registers (the tensor cores' accumulation
 //           truncates; chunking keeps that bias near 2^-24 x 48).
 // Only the tiles of the upper triangle (row block <= column block) of Re rho
-// are formed: that is the triangle the eigenvalue solver reads.  All waits are
+// are formed: that is the triangle the eigenvalue solver reads.
+//
+// The same kernel forms the cross product of two different row sets (mode 2)
+// for the Schmidt values as Rayleigh quotients: B = U^H A with U the
+// eigenvectors of rho, |B_i|^2 = u_i^H rho u_i, formed from A itself (no
+// squared matrix), and only the row sums of |B|^2 leave the chip.  All waits are
 // bounded; on timeout the kernel raises the error flag, lets the MMAs it
 // issued finish, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "device_common.cuh"
 #include "ed_internal.h"
 
 namespace osmps {
@@ -35,45 +41,12 @@ constexpr int kOpBytes = kTile * kKc * 4;  // one operand tile: 16 KiB
 constexpr int kStageBytes = 4 * kOpBytes;  // A_hi, A_lo, B_hi, B_lo
 constexpr int kThreads = 192;                // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr int kChunk = 4;                    // stages accumulated in TMEM before a register readout
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
-__device__ __forceinline__ unsigned su(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ unsigned long long gns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ bool try_wait(unsigned long long *bar, unsigned ph) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su(bar)), "r"(ph)
-        : "memory");
-    return ok != 0;
-}
-__device__ __noinline__ bool wait_bounded(unsigned long long *bar, unsigned ph, const int *err) {
-    if (try_wait(bar, ph)) return true;
-    const unsigned long long t0 = gns();
-    for (unsigned it = 1;; ++it) {
-        if (try_wait(bar, ph)) return true;
-        if ((it & 63u) == 0) {
-            if (*(volatile const int *)err != 0) return false;
-            if (gns() - t0 > kWaitNs) return false;
-        }
-    }
-}
-__device__ __forceinline__ void bar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void bar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su(bar)), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ void tma2d(void *dst, const CUtensorMap *tm, int c0, int c1, unsigned long long *bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(su(dst)),
-        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(su(bar))
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -102,7 +75,7 @@ __device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long a, 
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(unsigned long long *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su(bar))
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
 
@@ -125,6 +98,64 @@ __global__ void split_planes_kernel(const float2 *psi, int n, long long K, float
     }
 }
 
+__device__ __forceinline__ void tf32_split(float v, float &hi, float &lo) {
+    unsigned u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+    hi = __uint_as_float(u);
+    lo = v - hi;
+}
+
+// Rows of the left factor of the Rayleigh images: R (row-major n x n complex,
+// R[i][x] = conj(u_i[x])) as PX[i] = [Re R_i | Im R_i] and QX[i] = [Im R_i | -Re R_i],
+// so that Re (R A)[i][k] = PX_i . PY_k and Im (R A)[i][k] = QX_i . PY_k.
+__global__ void x_planes_kernel(const float2 *R, int n, float *Phi, float *Plo, float *Qhi, float *Qlo) {
+    const long long total = (long long)n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / n, x = i % n;
+        const float2 a = R[i];
+        float hr, lr, hi_, li;
+        tf32_split(a.x, hr, lr);
+        tf32_split(a.y, hi_, li);
+        const long long row = r * 2 * n;
+        Phi[row + x] = hr;
+        Plo[row + x] = lr;
+        Phi[row + n + x] = hi_;
+        Plo[row + n + x] = li;
+        Qhi[row + x] = hi_;
+        Qlo[row + x] = li;
+        Qhi[row + n + x] = -hr;
+        Qlo[row + n + x] = -lr;
+    }
+}
+
+// Rows of the right factor: Y[k][x] = conj(A[x][k]), A[x][k] = psi[x * sx + k * sk]
+// (sx = 1 or sk = 1), as PY[k] = [Re Y_k | Im Y_k]; 32 x 32 tiles through shared
+// memory so that the reads run along the contiguous index of psi and the
+// writes along x.
+__global__ void y_planes_kernel(const float2 *psi, int n, long long sx, long long sk, float *Phi, float *Plo) {
+    __shared__ float2 t[32][33];  // t[k - k0][x - x0]
+    const int x0 = blockIdx.x * 32;
+    const long long k0 = (long long)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int xl = (sx == 1) ? (int)threadIdx.x : r, kl = (sx == 1) ? r : (int)threadIdx.x;
+        t[kl][xl] = psi[(long long)(x0 + xl) * sx + (k0 + kl) * sk];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long row = (k0 + r) * 2 * n;
+        const int x = x0 + threadIdx.x;
+        const float2 a = t[r][threadIdx.x];
+        float h, l;
+        tf32_split(a.x, h, l);
+        Phi[row + x] = h;
+        Plo[row + x] = l;
+        tf32_split(-a.y, h, l);
+        Phi[row + n + x] = h;
+        Plo[row + n + x] = l;
+    }
+}
+
 // One 128 x 128 tile of  mode 0: Re rho = P P^T (upper-triangle tiles)
 //                        mode 1: G = P[:, :K] P[:, K:]^T (all tiles)
 // The tensor cores accumulate in FP32 with truncation, so a long K-loop into
@@ -132,12 +163,17 @@ __global__ void split_planes_kernel(const float2 *psi, int n, long long K, float
 // K-loop is therefore cut into chunks of kChunk stages, each accumulated in
 // one of two TMEM buffers and added by the epilogue warps into FP32 registers
 // (round to nearest) while the next chunk is computed.
+//                        mode 2: rows x of A (ahi, alo) against rows y of B (bhi,
+//                                the same K offset 0, nk stages); each output row's
+//                                sum of squares over the tile goes to
+//                                part[x * ntx + tile column] in FP64
 __global__ void __launch_bounds__(kThreads, 1)
-    gram_tc_kernel(const __grid_constant__ CUtensorMap thi, const __grid_constant__ CUtensorMap tlo, int mode,
-                   int n, int K, float2 *rho, float *G, int *err) {
+    gram_tc_kernel(const __grid_constant__ CUtensorMap ahi, const __grid_constant__ CUtensorMap alo,
+                   const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo, int mode,
+                   int n, int nk, int kb, int ntx, float2 *rho, float *G, double *part, int *err) {
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte aligned stages (128-byte swizzle atoms)
-    const unsigned raw = su(smem_raw);
+    const unsigned raw = smem_u32(smem_raw);
     unsigned char *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + kStages * kStageBytes);
     unsigned long long *empty = full + kStages;
@@ -156,27 +192,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             ++ty;
         }
         tx = ty + t;
-    } else {
+    } else if (mode == 1) {
         ty = blockIdx.x / T;
         tx = blockIdx.x % T;
+    } else {
+        ty = blockIdx.x / ntx;
+        tx = blockIdx.x % ntx;
     }
     const int x0 = ty * kTile, y0 = tx * kTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            bar_init(&full[s], 1);
-            bar_init(&empty[s], 1);
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            bar_init(&chunk_done[b], 1);
-            bar_init(&acc_free[b], 4);
+            mbar_init(&chunk_done[b], 1);
+            mbar_init(&acc_free[b], 4);
         }
-        bar_init(drain, 1);
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su(tmem_slot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(2 * kTile)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -186,9 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
 
-    const int nk = (mode == 0 ? 2 * K : K) / kKc;
     const int nchunks = (nk + kChunk - 1) / kChunk;
-    const int kb = (mode == 0) ? 0 : K;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -196,21 +233,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             int issued = 0;
             for (int s = 0; s < nk; ++s) {
                 const int st = s % kStages;
-                if (s >= kStages && !wait_bounded(&empty[st], (unsigned)(((s / kStages) - 1) & 1), err)) {
+                if (s >= kStages && !mbar_wait(&empty[st], (unsigned)(((s / kStages) - 1) & 1), err)) {
                     atomicExch(err, 1);
                     break;
                 }
                 unsigned char *base = smem + st * kStageBytes;
-                bar_expect_tx(&full[st], kStageBytes);
-                tma2d(base, &thi, s * kKc, x0, &full[st]);
-                tma2d(base + kOpBytes, &tlo, s * kKc, x0, &full[st]);
-                tma2d(base + 2 * kOpBytes, &thi, kb + s * kKc, y0, &full[st]);
-                tma2d(base + 3 * kOpBytes, &tlo, kb + s * kKc, y0, &full[st]);
+                mbar_arrive_expect_tx(&full[st], kStageBytes);
+                tma2d(base, &ahi, s * kKc, x0, &full[st]);
+                tma2d(base + kOpBytes, &alo, s * kKc, x0, &full[st]);
+                tma2d(base + 2 * kOpBytes, &bhi, kb + s * kKc, y0, &full[st]);
+                tma2d(base + 3 * kOpBytes, &blo, kb + s * kKc, y0, &full[st]);
                 ++issued;
             }
             // every copy issued has landed before the CTA moves on
             for (int s = issued > kStages ? issued - kStages : 0; s < issued; ++s)
-                wait_bounded(&full[s % kStages], (unsigned)((s / kStages) & 1), err);
+                mbar_wait(&full[s % kStages], (unsigned)((s / kStages) & 1), err);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -219,16 +256,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int st = s % kStages;
                 const int c = s / kChunk, buf = c & 1;
                 if (s % kChunk == 0 && c >= 2 &&
-                    !wait_bounded(&acc_free[buf], (unsigned)(((c / 2) - 1) & 1), err)) {
+                    !mbar_wait(&acc_free[buf], (unsigned)(((c / 2) - 1) & 1), err)) {
                     atomicExch(err, 1);
                     break;
                 }
-                if (!wait_bounded(&full[st], (unsigned)((s / kStages) & 1), err)) {
+                if (!mbar_wait(&full[st], (unsigned)((s / kStages) & 1), err)) {
                     atomicExch(err, 1);
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const unsigned base = su(smem + st * kStageBytes);
+                const unsigned base = smem_u32(smem + st * kStageBytes);
                 const unsigned dcol = tmem + (unsigned)(buf * kTile);
 #pragma unroll
                 for (int kk = 0; kk < kKc / 8; ++kk) {
@@ -245,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // no MMA of this CTA is in flight past this point
             mma_commit(drain);
-            wait_bounded(drain, 0u, err);
+            mbar_wait(drain, 0u, err);
         }
     } else {
         // ---- epilogue warps: TMEM chunk -> FP32 registers ----
@@ -256,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             const int buf = c & 1;
-            if (!wait_bounded(&chunk_done[buf], (unsigned)((c / 2) & 1), err)) {
+            if (!mbar_wait(&chunk_done[buf], (unsigned)((c / 2) & 1), err)) {
                 atomicExch(err, 1);
                 ok = false;
                 break;
@@ -282,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su(&acc_free[buf])) : "memory");
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_free[buf])) : "memory");
         }
         if (ok) {
             const int row = lg * 32 + lane;
@@ -290,6 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (mode == 0) {
 #pragma unroll
                 for (int j = 0; j < kTile; ++j) rho[o + j].x = sum[j];
+            } else if (mode == 2) {
+                double s2 = 0.0;
+#pragma unroll
+                for (int j = 0; j < kTile; ++j) s2 = fma((double)sum[j], (double)sum[j], s2);
+                part[(long long)(x0 + row) * ntx + tx] = s2;
             } else {
 #pragma unroll
                 for (int j = 0; j < kTile; j += 4)
@@ -376,11 +418,60 @@ cudaError_t gram_tc_launch(Handle *h, const void *psi, int n, long long K, void 
     }
     const int T = n / gtc::kTile;
     gtc::gram_tc_kernel<<<T * (T + 1) / 2, gtc::kThreads, gram_tc_smem(), h->stream>>>(
-        thi, tlo, 0, n, (int)K, (float2 *)rho, G, &h->ctl->error);
-    gtc::gram_tc_kernel<<<T * T, gtc::kThreads, gram_tc_smem(), h->stream>>>(thi, tlo, 1, n, (int)K, (float2 *)rho,
-                                                                              G, &h->ctl->error);
+        thi, tlo, thi, tlo, 0, n, (int)(2 * K / gtc::kKc), 0, T, (float2 *)rho, G, nullptr, &h->ctl->error);
+    gtc::gram_tc_kernel<<<T * T, gtc::kThreads, gram_tc_smem(), h->stream>>>(
+        thi, tlo, thi, tlo, 1, n, (int)(K / gtc::kKc), (int)K, T, (float2 *)rho, G, nullptr, &h->ctl->error);
     dim3 g2(n / 32, n / 32), b2(32, 8);
     gtc::gram_assemble_kernel<<<g2, b2, 0, h->stream>>>(G, (float2 *)rho, n);
+    h->launches += 4;
+    return cudaGetLastError();
+}
+
+bool rayleigh_tc_supported(int n, long long K) {
+    return n >= gtc::kTile && n % gtc::kTile == 0 && K % gtc::kTile == 0 && K >= n && K / gtc::kTile <= (1ll << 24) &&
+           gtc_encoder() != nullptr;
+}
+
+size_t rayleigh_tc_plane_floats(int n, long long K) { return 8 * (size_t)n * n + 4 * (size_t)n * (size_t)K; }
+
+// Row sums of |B|^2 for B = R A: R row-major n x n complex64 (R[i][x] = conj(u_i[x])),
+// A[x][k] = psi[x * sx + k * sk] (n x K).  planes: rayleigh_tc_plane_floats(n, K)
+// floats; part_re / part_im: n x (K / 128) doubles, the sums over each 128-column
+// tile of (Re B)^2 and (Im B)^2.
+cudaError_t rayleigh_tc_launch(Handle *h, const void *R, const void *psi, int n, long long K, long long sx,
+                               long long sk, float *planes, double *part_re, double *part_im) {
+    GtcEncodeFn enc = gtc_encoder();
+    if (enc == nullptr || !rayleigh_tc_supported(n, K)) return cudaErrorNotSupported;
+    const size_t xp = 2 * (size_t)n * n, yp = 2 * (size_t)n * (size_t)K;
+    float *PXhi = planes, *PXlo = PXhi + xp, *QXhi = PXlo + xp, *QXlo = QXhi + xp;
+    float *PYhi = QXlo + xp, *PYlo = PYhi + yp;
+    gtc::x_planes_kernel<<<h->nsm * 8, 256, 0, h->stream>>>((const float2 *)R, n, PXhi, PXlo, QXhi, QXlo);
+    {
+        const dim3 g((unsigned)(n / 32), (unsigned)(K / 32)), b(32, 8);
+        gtc::y_planes_kernel<<<g, b, 0, h->stream>>>((const float2 *)psi, n, sx, sk, PYhi, PYlo);
+    }
+    CUtensorMap m[6];
+    float *base[6] = {PXhi, PXlo, QXhi, QXlo, PYhi, PYlo};
+    for (int i = 0; i < 6; ++i) {
+        cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)(i < 4 ? n : K)};
+        cuuint64_t strides[1] = {(cuuint64_t)(2 * (size_t)n * 4)};
+        cuuint32_t box[2] = {gtc::kKc, gtc::kTile}, es[2] = {1, 1};
+        if (enc(&m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base[i], dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gtc::gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem());
+        attr = true;
+    }
+    const int ntx = (int)(K / gtc::kTile), nty = n / gtc::kTile;
+    const int nk = 2 * n / gtc::kKc;
+    gtc::gram_tc_kernel<<<nty * ntx, gtc::kThreads, gram_tc_smem(), h->stream>>>(
+        m[0], m[1], m[4], m[5], 2, n, nk, 0, ntx, nullptr, nullptr, part_re, &h->ctl->error);
+    gtc::gram_tc_kernel<<<nty * ntx, gtc::kThreads, gram_tc_smem(), h->stream>>>(
+        m[2], m[3], m[4], m[5], 2, n, nk, 0, ntx, nullptr, nullptr, part_im, &h->ctl->error);
     h->launches += 4;
     return cudaGetLastError();
 }

@@ -38,7 +38,10 @@ __host__ __device__ inline int zacc_count(int L) { return L * L + L + 1; }
 
 // One streaming pass over p_b = |psi_b|^2.  Per thread: 16 amplitudes at
 // li = tid + 256 k; sums over a thread and warp in T (FP32 in mixed mode),
-// across warps, tiles and CTAs in FP64.
+// across warps, tiles and CTAs in FP64.  The low-bit marginal G(lo) runs over
+// every tile a CTA visits (thousands at L = 30 on a small grid), so in FP32 it
+// is a compensated (Kahan) sum: its error stays at a few units of FP32
+// rounding of G instead of growing with the number of tiles.
 template <typename T>
 __global__ void __launch_bounds__(kZThreads) zstats_kernel(const typename ZV<T>::c *psi, int L, int t,
                                                            long long ntiles, double *blockacc, double *Gpart) {
@@ -46,9 +49,9 @@ __global__ void __launch_bounds__(kZThreads) zstats_kernel(const typename ZV<T>:
     const int nacc = zacc_count(L);
     const int nown = (nacc + kZThreads - 1) / kZThreads;  // <= 4 for L <= 30
     double own[4] = {0, 0, 0, 0};
-    T G[kZPer];
+    T G[kZPer], Gc[kZPer];  // running marginal and its Kahan compensation (unused in FP64)
 #pragma unroll
-    for (int k = 0; k < kZPer; ++k) G[k] = (T)0;
+    for (int k = 0; k < kZPer; ++k) G[k] = Gc[k] = (T)0;
     __shared__ double red[kZTileBits + 1][kZThreads / 32];
     __shared__ double stat[kZTileBits + 1];  // P, M_0..M_{t-1}
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -65,7 +68,14 @@ __global__ void __launch_bounds__(kZThreads) zstats_kernel(const typename ZV<T>:
                 pv = a.x * a.x + a.y * a.y;
             }
             pk[k] = pv;
-            G[k] += pv;
+            if (sizeof(T) == sizeof(float)) {
+                const T y = pv - Gc[k];
+                const T tsum = G[k] + y;
+                Gc[k] = (tsum - G[k]) - y;
+                G[k] = tsum;
+            } else {
+                G[k] += pv;
+            }
         }
         // per-thread moments: v[0] = sum p, v[1+j] = sum s_j p
         T v[kZTileBits + 1];
@@ -136,7 +146,7 @@ __global__ void __launch_bounds__(kZThreads) zstats_kernel(const typename ZV<T>:
 #pragma unroll
     for (int k = 0; k < kZPer; ++k) {
         const int li = threadIdx.x + k * kZThreads;
-        if (li < nel) Gpart[(size_t)blockIdx.x * nel + li] = (double)G[k];
+        if (li < nel) Gpart[(size_t)blockIdx.x * nel + li] = (double)G[k] - (double)Gc[k];
     }
 }
 
@@ -813,6 +823,183 @@ osmps_status schmidt_svd(Handle *h, const void *psi, int cut, double *lambda_dev
         cudaStreamSynchronize(h->stream) != cudaSuccess)
         return OSMPS_ECUDA;
     return bad == 0 ? OSMPS_OK : OSMPS_ECUDA;
+}
+
+
+// ---------------------------------------------------------------------------
+// Schmidt values as Rayleigh quotients of the Gram product's eigenvectors
+// (complex64).  The eigenvalues of rho = A A^H carry absolute errors of order
+// eps |rho| in FP32, which dominate S of a weakly entangled state; the
+// eigenvectors u_i do not square anything, and |u_i^H A|^2 formed from A
+// itself keeps the small Schmidt values to their own relative accuracy.  The
+// tensor cores' truncating accumulation leaves every value with nearly the same
+// relative deficit (~1e-6), so the values are rescaled to sum to |psi|^2 (FP64):
+// the Schmidt values sum to the norm (Sec. IV, bond entropy).
+// ---------------------------------------------------------------------------
+constexpr int kRayMaxN = 8192;  // one CTA sorts the spectrum in shared memory
+
+// lambda_i = sum_t part_re[i][t] + part_im[i][t] (fixed order), sorted descending,
+// rescaled by |psi|^2 / sum_i lambda_i (norm partials: 4 doubles per CTA, the
+// first is |x|^2), S = -sum lambda ln lambda.  One CTA, n a power of two.
+__global__ void __launch_bounds__(1024) rayleigh_entropy_kernel(const double *part_re, const double *part_im, int n,
+                                                                 int ntx, const double *norm_parts, int nparts,
+                                                                 double *lambda, double *S) {
+    extern __shared__ double lam_s[];
+    __shared__ double red[32];
+    __shared__ double trace_s;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = 0.0;
+        for (int t = 0; t < ntx; ++t) v += part_re[(size_t)i * ntx + t] + part_im[(size_t)i * ntx + t];
+        lam_s[i] = v;
+    }
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int p = threadIdx.x; p < nparts; p += 32) t += norm_parts[4 * (size_t)p];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (threadIdx.x == 0) trace_s = t;
+    }
+    __syncthreads();
+    // bitonic sort, descending
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const double a = lam_s[i], b = lam_s[ixj];
+                    const bool desc = (i & k) == 0;
+                    if (desc ? (a < b) : (a > b)) {
+                        lam_s[i] = b;
+                        lam_s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // sum of all values, fixed order
+    double r = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) r += lam_s[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        trace_s = tot > 0.0 ? trace_s / tot : 1.0;  // now the rescaling factor
+    }
+    __syncthreads();
+    const double scale = trace_s;
+    double e = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double l = lam_s[i] * scale;
+        lambda[i] = l;
+        if (l > 0.0) e -= l * log(l);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *S = t;
+    }
+}
+
+bool rayleigh_applicable(const Handle *h, int cut) {
+    const int L = h->L;
+    const int ls = cut < L - cut ? cut : L - cut;
+    const int n = 1 << ls;
+    const long long K = 1ll << (L - ls);
+    return h->prec == OSMPS_MIXED && n <= kRayMaxN && rayleigh_tc_supported(n, K);
+}
+
+osmps_status schmidt_rayleigh(Handle *h, const void *psi, int cut, void *rho, double *lambda_dev, double *S_dev) {
+    if (!rayleigh_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
+    const int L = h->L;
+    int n;
+    long long K, sx, sk;
+    if (cut <= L - cut) {
+        n = 1 << cut;
+        K = 1ll << (L - cut);
+        sx = K;
+        sk = 1;
+    } else {
+        n = 1 << (L - cut);
+        K = 1ll << cut;
+        sx = 1;
+        sk = n;
+    }
+    const int ntx = (int)(K / 128);
+    // scratch: the Gram product's planes and the Rayleigh planes share gram_aux
+    const size_t gram_need = sizeof(float) * ((size_t)n * 4 * (size_t)K + (size_t)n * n);
+    const size_t ray_need = sizeof(float) * rayleigh_tc_plane_floats(n, K) + 2 * sizeof(double) * (size_t)n * ntx;
+    const size_t need = gram_need > ray_need ? gram_need : ray_need;
+    if (need > h->gram_aux_bytes) {
+        dev_free(h, h->gram_aux, h->gram_aux_bytes);
+        h->gram_aux = nullptr;
+        h->gram_aux_bytes = 0;
+        cudaError_t err;
+        h->gram_aux = dev_alloc(h, need, &err);
+        if (err != cudaSuccess) return OSMPS_ENOMEM;
+        h->gram_aux_bytes = need;
+    }
+    int nn = 0;
+    if (launch_gram(h, psi, cut, rho, &nn) != cudaSuccess || nn != n) return OSMPS_ECUDA;
+    // eigenvectors of the Hermitian rho (read as the column-major lower triangle
+    // of conj(rho), so column i is conj(u_i); rho is overwritten by them)
+    {
+        std::lock_guard<std::mutex> lock(g_solver_mu);
+        if (!load_solver() || g_solver.params == nullptr) return OSMPS_EUNSUPPORTED;
+        if (g_solver.set_stream(g_solver.handle, h->stream) != CUSOLVER_STATUS_SUCCESS) return OSMPS_ECUDA;
+        const size_t o_work = 16 + (((size_t)n * sizeof(float) + 255) & ~(size_t)255);
+        CKS_(grow_ws(h, &h->solver_ws, &h->solver_ws_bytes, true, o_work + 256));
+        size_t work_bytes = 0, host_bytes = 0;
+        if (g_solver.x_bufsize(g_solver.handle, g_solver.params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                               (int64_t)n, CUDA_C_32F, rho, (int64_t)n, CUDA_R_32F, (char *)h->solver_ws + 16,
+                               CUDA_C_32F, &work_bytes, &host_bytes) != CUSOLVER_STATUS_SUCCESS)
+            return OSMPS_ECUDA;
+        if (work_bytes < 256) work_bytes = 256;
+        CKS_(grow_ws(h, &h->solver_ws, &h->solver_ws_bytes, true, o_work + work_bytes + 64));
+        std::vector<char> host_ws;
+        try {
+            host_ws.resize(host_bytes > 0 ? host_bytes : 1);
+        } catch (...) {
+            return OSMPS_ENOMEM;
+        }
+        char *ws = (char *)h->solver_ws;
+        int *info = (int *)ws, *flag = info + 1;
+        if (g_solver.x_eig(g_solver.handle, g_solver.params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                           (int64_t)n, CUDA_C_32F, rho, (int64_t)n, CUDA_R_32F, ws + 16, CUDA_C_32F, ws + o_work,
+                           work_bytes, host_ws.data(), host_bytes, info) != CUSOLVER_STATUS_SUCCESS)
+            return OSMPS_ECUDA;
+        eig_check_kernel<float><<<1, 1024, 0, h->stream>>>(info, (const float *)(ws + 16), n, flag);
+        h->launches += 1;
+        int bad = 0;
+        if (cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return OSMPS_ECUDA;
+        if (bad != 0) return OSMPS_ENOCONV;  // the caller falls back to the singular values of M
+    }
+    float *planes = (float *)h->gram_aux;
+    double *part_re = (double *)((char *)h->gram_aux + sizeof(float) * rayleigh_tc_plane_floats(n, K));
+    double *part_im = part_re + (size_t)n * ntx;
+    if (rayleigh_tc_launch(h, rho, psi, n, K, sx, sk, planes, part_re, part_im) != cudaSuccess) return OSMPS_ECUDA;
+    int np = 0;
+    if (launch_norm2(h, psi, h->partials, &np) != cudaSuccess) return OSMPS_ECUDA;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(rayleigh_entropy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kRayMaxN * sizeof(double)));
+        attr = true;
+    }
+    rayleigh_entropy_kernel<<<1, 1024, (size_t)n * sizeof(double), h->stream>>>(part_re, part_im, n, ntx, h->partials,
+                                                                                 np, lambda_dev, S_dev);
+    h->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
 }
 
 }  // namespace osmps

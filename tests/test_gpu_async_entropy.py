@@ -1,5 +1,7 @@
 """Asynchronous bond entropy (Gram on the caller's stream, eigen-solve on the
-handle's side stream) against the synchronous call and the oracle."""
+handle's side stream) against the synchronous call and the oracle.  The
+asynchronous call takes the Gram route (eigenvalues of rho), so the
+synchronous results it is compared with take it too (entropy method 0)."""
 import numpy as np
 import pytest
 import torch
@@ -24,11 +26,12 @@ def launches(c):
     return n.value
 
 
-@pytest.mark.parametrize("prec,atol", [("fp64", 1e-12), ("mixed", 2e-5)])
+@pytest.mark.parametrize("prec,atol", [("fp64", 1e-12), ("mixed", 1e-5)])
 def test_async_matches_sync_and_oracle(prec, atol):
     L = 12
     psi = si.gaussian_state(L, 7)
     c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+    c.set_entropy_method(0)
     x = to_dev(psi, prec)
     S_sync, lam_sync = c.schmidt_entropy(x, cut=5, spectrum=True)
     p = c.schmidt_entropy_async(x, cut=5, spectrum=True)
@@ -50,6 +53,7 @@ def test_async_pipeline_with_state_overwritten(prec):
     result equals the synchronous entropy of the state it was enqueued on."""
     L = 16
     c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+    c.set_entropy_method(0)
     x = c.new_state()
     c.init_basis_state(x, 0)
     snaps, pend = [], []
@@ -74,6 +78,7 @@ def test_async_at_full_size_cut_half():
     """L = 24 complex64 (n = 4096 Schmidt values): async equals sync."""
     L = 24
     c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    c.set_entropy_method(0)
     x = c.new_state()
     c.init_basis_state(x, 0)
     c.krylov_evolve(x, 0.1, 3, 20)
@@ -159,13 +164,14 @@ def test_own_solver_page_value_and_special_states(prec):
     c.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_own_solver_pipeline_against_library(prec, tol):
     """Three overlapped measurements along an evolution on the own solver (two
     slots, the third call waits for the first), each against the library
     solver's synchronous entropy of the same stored state."""
     L = 16
     c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+    c.set_entropy_method(0)
     c.set_async_eigensolver(16)
     x = c.new_state()
     c.init_basis_state(x, 0)
@@ -188,10 +194,14 @@ def test_own_solver_pipeline_against_library(prec, tol):
 
 def test_own_solver_full_size_quench():
     """L = 24 complex64 quench state (n = 4096): own solver on 16 CTAs against the
-    library solver: the Schmidt values above 1e-4 to 2e-6, S to the FP32 noise
-    floor of the tiny eigenvalues."""
+    library solver on the same Gram product: the Schmidt values above 1e-4 to
+    2e-6 and the trace.  Both are FP32 eigen-solvers of the FP32 Gram product,
+    whose thousands of eigenvalues below 1e-7 are noise at that level; S of
+    such a state is taken from the default (Rayleigh) route instead, which is
+    checked against the FP64 form in test_gpu_entropy_rayleigh.py."""
     L = 24
     c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    c.set_entropy_method(0)
     x = c.new_state()
     c.init_basis_state(x, 0)
     c.krylov_evolve(x, 0.1, 5, 20)
@@ -199,6 +209,5 @@ def test_own_solver_full_size_quench():
     S, lam = own_entropy(c, x, -1, 16)
     big = lam_lib > 1e-4
     np.testing.assert_allclose(lam[big], lam_lib[big], atol=2e-6)
-    assert abs(lam.sum() - 1.0) < 1e-4
-    assert abs(S - S_lib) < 5e-3
+    assert abs(lam.sum() - 1.0) < 1e-5
     c.close()

@@ -169,7 +169,7 @@ def test_lrqi_quench_short_horizon_vs_oracle(prec):
         np.testing.assert_allclose(c.measure_local(x), O.measure_local(ref, L), atol=tol)
         np.testing.assert_allclose(c.measure_corr(x), O.measure_corr(ref, L), atol=tol)
         S = c.schmidt_entropy(x)
-        assert abs(S - O.schmidt_entropy(ref, L)) < tol * max(1.0, S) * 10
+        assert abs(S - O.schmidt_entropy(ref, L)) < tol * max(1.0, S)
 
 
 def test_lrqi_quench_L24_two_steps_vs_oracle():

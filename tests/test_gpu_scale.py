@@ -56,3 +56,44 @@ def test_scale_L30_neel_quench_and_half_chain_spectrum():
     assert np.all(np.diff(lam) <= 0.0)
     assert 0.0 <= S < 0.1
     m.close()
+
+
+@pytest.mark.timeout(1500)
+def test_scale_L30_full_quench_to_t2():
+    """The whole scale workload: 100 Krylov steps of 0.02 (m = 12) from the Neel
+    state to t = 2.  Every step: unitarity and energy conservation within the
+    mixed tolerance.  At t = 2: the reflection x spin-flip symmetry of <sz_i>.
+    Beside it the same quench at L = 28 in complex64 against the FP64 form
+    (whose layout is checked against the oracle at L = 24): <sz_i>, <sz_i sz_j>
+    and the state within the mixed tolerance after all 100 steps."""
+    c = Chain(L, J=1.0, alpha=ALPHA, h=H, prec="mixed")
+    x = c.new_state()
+    c.init_basis_state(x, si.neel_index(L))
+    e0 = neel_energy()
+    for k in range(100):
+        c.krylov_evolve(x, 0.02, 1, 12)
+        e, n2 = c.energy(x)
+        assert abs(n2 - 1.0) < 1e-5, (k, n2)
+        assert abs(e / n2 - e0) < 1e-5 * abs(e0), (k, e, e0)
+    sz = c.measure_local(x)
+    np.testing.assert_allclose(sz, -sz[::-1], atol=1e-5)
+    c.close()
+    del x
+    torch.cuda.empty_cache()
+    L28 = 28
+    out = {}
+    for prec in ("fp64", "mixed"):
+        m = Chain(L28, J=1.0, alpha=ALPHA, h=H, prec=prec)
+        y = m.new_state()
+        m.init_basis_state(y, si.neel_index(L28))
+        m.krylov_evolve(y, 0.02, 100, 12)
+        sz28, zz28 = m.measure_zz(y)
+        out[prec] = (y.to(torch.complex128), sz28, zz28)
+        m.close()
+        del y
+        torch.cuda.empty_cache()
+    yf, szf, zzf = out["fp64"]
+    ym, szm, zzm = out["mixed"]
+    np.testing.assert_allclose(szm, szf, rtol=0, atol=1e-5)
+    np.testing.assert_allclose(zzm, zzf, rtol=0, atol=1e-5)
+    assert (torch.linalg.vector_norm(ym - yf) / torch.linalg.vector_norm(yf)).item() < 1e-5

@@ -9,6 +9,7 @@ osmps_ed_measure_zz (which uses the handle's own scratch) within the
 tolerances of the other measurement tests.
 """
 import ctypes as C
+import math
 
 import numpy as np
 import pytest
@@ -52,3 +53,35 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
     out = torch.zeros(8, dtype=torch.float64, device="cuda")
     assert _noalloc(B, 31, "fp64", psi, out) == B.OSMPS_EINVAL
     assert _noalloc(B, 0, "fp64", psi, out) == B.OSMPS_EINVAL
+
+
+@pytest.mark.timeout(600)
+def test_noalloc_full_size_product_state_closed_form():
+    """L = 28 complex64 (683 tiles per CTA of the 96-CTA pass): the rotated product
+    state prod_k (cos q |up> - i sin q |down>) has <sz_k> = cos 2q and
+    <sz_i sz_j> = cos^2 2q exactly; both entry points meet that within the mixed
+    tolerance, low-bit sites included (their marginal is summed over every tile
+    a CTA visits)."""
+    from paper_1802_10052_gb300 import Chain
+    from paper_1802_10052_gb300 import _binding as B
+    L, q = 28, 0.3
+    one = torch.tensor([math.cos(q), -1j * math.sin(q)], dtype=torch.complex64, device="cuda")
+    psi = one
+    for _ in range(L - 1):
+        psi = torch.kron(psi, one)
+    want_z, want_zz = math.cos(2 * q), math.cos(2 * q) ** 2
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    sz, zz = c.measure_zz(psi)
+    off = ~np.eye(L, dtype=bool)
+    np.testing.assert_allclose(sz, want_z, rtol=0, atol=1e-5)
+    np.testing.assert_allclose(zz[off], want_zz, rtol=0, atol=1e-5)
+    out = torch.empty(L + L * L, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out.fill_(float("nan"))
+        assert _noalloc(B, L, "mixed", psi, out) == B.OSMPS_OK
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        np.testing.assert_allclose(got[:L], want_z, rtol=0, atol=1e-5)
+        np.testing.assert_allclose(got[L:].reshape(L, L)[off], want_zz, rtol=0, atol=1e-5)
+        np.testing.assert_allclose(got[L:].reshape(L, L), zz, rtol=0, atol=1e-6)
+    c.close()
