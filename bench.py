@@ -47,12 +47,14 @@ def parse():
     ap.add_argument("--no-trotter", action="store_true")
     ap.add_argument("--no-rdm", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true")
+    ap.add_argument("--no-scale", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--entropy", choices=["async", "sync"], default="sync",
                     help="bond entropy per step: overlapped eigen-solve (async) or blocking (sync)")
     ap.add_argument("--main-priority", choices=["high", "default"], default="high",
                     help="priority of the stream the evolution runs on")
-    ap.add_argument("--profile-case", choices=["batch_L16", "gates_L24", "rdm_L24"], default=None,
+    ap.add_argument("--profile-case", choices=["batch_L16", "gates_L24", "rdm_L24", "hpsi_L27", "quench_L24"],
+                    default=None,
                     help="run one small profiling workload and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -129,8 +131,8 @@ def measured_peaks():
         return None
 
 
-def traffic_record():
-    """ncu DRAM traffic of the H.psi passes, valid only for the kernel source it was taken on."""
+def traffic_record(L, prec):
+    """ncu DRAM traffic of one H.psi product at size L, valid only for the kernel source it was taken on."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "hpsi_traffic.json")))
     except Exception:
@@ -138,7 +140,10 @@ def traffic_record():
     src = open(os.path.join(ROOT, "paper_1802_10052_gb300", "csrc", "hpsi_kernels.cu"), "rb").read()
     if rec.get("hpsi_kernels_sha1") != hashlib.sha1(src).hexdigest():
         return None
-    return rec
+    for r in rec.get("records", []):
+        if r.get("L") == L and r.get("prec") == prec:
+            return r
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -492,6 +497,53 @@ def trotter_nn(L=24, reps=10):
     return out
 
 
+def scale_L30():
+    """The scale workload: H = sum |i-j|^-1 sz sz + 1.2 sum sx, L = 30, complex64, Krylov
+    dimension 12, from the Neel state to t = 2 in 100 steps of 0.02 (seconds per unit of
+    simulated time, CUDA events), the H.psi product at L = 30 (GB/s), and the half-chain
+    spectrum at t = 2 through the tensor-core Gram product of 32768 x 32768 and its
+    eigenvalues; unitarity and energy conservation at t = 2."""
+    import torch
+
+    import seeded_inputs as si
+    from paper_1802_10052_gb300 import Chain
+
+    L, alpha, h, dt, m, n = 30, 1.0, 1.2, 0.02, 12, 100
+    c = Chain(L, J=1.0, alpha=alpha, h=h, prec="mixed")
+    x = c.new_state()
+    c.init_basis_state(x, si.neel_index(L))
+    e0 = sum((L - r) * (-1) ** r / r ** alpha for r in range(1, L))
+    torch.cuda.synchronize()
+    c.timing_read(reset=True)
+    c.timing_enable(True)
+    e_0, e_1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_0.record()
+    c.krylov_evolve(x, dt, n, m)
+    e_1.record()
+    torch.cuda.synchronize()
+    hp_ms, hp_n = c.timing_read(reset=True)
+    c.timing_enable(False)
+    ms = e_0.elapsed_time(e_1)
+    E, n2 = c.energy(x)
+    t0 = time.perf_counter()
+    S, lam = c.schmidt_entropy(x, spectrum=True)
+    t_ent = time.perf_counter() - t0
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    alg = 2.0 * (1 << L) * 8
+    t_hp = hp_ms / max(hp_n, 1)
+    out = {"workload": "H = sum |i-j|^-1 sz sz + 1.2 sum sx, L=30, complex64, Neel start, Krylov m=12, "
+                       "100 steps of dt=0.02 to t=2",
+           "s_per_unit_time": ms * 1e-3 / (n * dt), "hpsi_ms_per_product": t_hp,
+           "hpsi_algorithmic_GBps": alg / (t_hp * 1e-3) / 1e9, "hpsi_frac_of_measured_hbm": alg / (t_hp * 1e-3) / 1e9 / peak,
+           "entropy_s": t_ent, "entropy_route": "tensor-core Gram 32768 x 32768 + eigenvalues", "S_t2": S,
+           "lambda0_t2": float(lam[0]), "norm_err_t2": abs(n2 - 1.0), "energy_rel_err_t2": abs(E / n2 - e0) / abs(e0)}
+    c.close()
+    del x
+    torch.cuda.empty_cache()
+    return out
+
+
 def rdm_L24(reps=3):
     """All 276 two-site RDMs and the bond entropy of all 23 cuts of an L = 24 complex64
     state (the quench state after 0.2 time units): ms per call.  The pair kernel reads
@@ -720,6 +772,39 @@ def profile_case(name):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": name, "norm": float(torch.linalg.vector_norm(x).item())}))
         c.close()
+    elif name == "hpsi_L27":
+        # H.psi at L = 27 (alpha = 1.5, h = 0.8), complex64, seeded Gaussian state drawn on the
+        # device: the first three-pass size; two products (3 GB on the device)
+        from paper_1802_10052_gb300 import Chain
+        L = 27
+        c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+        g = torch.Generator(device="cuda")
+        g.manual_seed(27)
+        x = torch.complex(torch.randn(1 << L, generator=g, device="cuda"), torch.randn(1 << L, generator=g, device="cuda"))
+        y = c.new_state()
+        c.apply_H(x, y)
+        c.apply_H(y, x)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "norm": float(torch.linalg.vector_norm(x).item())}))
+        c.close()
+    elif name == "quench_L24":
+        # the benchmark workload (10 Krylov steps, <sz>, <szsz>, S per step), complex64: five
+        # untimed steps to t = 0.5, then two steps inside the NVTX range "step" (for ncu --nvtx)
+        from paper_1802_10052_gb300 import Chain
+        c = Chain(WL["L"], J=WL["J"], alpha=WL["alpha"], h=WL["h"], prec="mixed")
+        x = c.new_state()
+        c.init_basis_state(x, 0)
+        for k in range(7):
+            if k == 5:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("step")
+            c.krylov_evolve(x, WL["dt"], WL["krylov_steps_per_step"], WL["m"])
+            c.measure_zz(x)
+            S = c.schmidt_entropy(x)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_case": name, "S": S}))
+        c.close()
     elif name == "rdm_L24":
         # L = 24 complex64 seeded Gaussian state: all 276 pair RDMs, twice
         from paper_1802_10052_gb300 import Chain
@@ -773,18 +858,18 @@ def main():
     D = 1 << WL["L"]
     alg24 = 2.0 * D * esize
     ach24 = alg24 / (res["hpsi_ms_avg"] * 1e-3) / 1e9 if res["hpsi_calls"] else None
+    t24 = traffic_record(WL["L"], args.prec)
     extra["roofline_L24"] = {"bound": "hbm", "achieved": ach24, "peak": peak, "unit": "GB/s",
                              "frac": ach24 / peak if ach24 else None, "algorithmic_bytes": alg24,
+                             "traffic": t24.get("dram_bytes_per_product") if t24 else None,
                              "kernel": "hpsi_pass_kernel (all passes of one H.psi product, in the timed step)"}
     roof = None
     if rank == 0 and not args.no_hpsi28:
         h28 = [hpsi_L28("mixed"), hpsi_L28("fp64", reps=6)]
         extra["hpsi_L28"] = h28
         r = h28[0] if args.prec == "mixed" else h28[1]
-        trec = traffic_record()
-        traffic = None
-        if trec and trec.get("prec") == args.prec and trec.get("L") == 28:
-            traffic = trec.get("dram_bytes_per_product")
+        trec = traffic_record(28, args.prec)
+        traffic = trec.get("dram_bytes_per_product") if trec else None
         roof = {"bound": "hbm", "achieved": r["algorithmic_GBps"], "peak": peak, "unit": "GB/s",
                 "frac": r["algorithmic_GBps"] / peak, "traffic": traffic,
                 "kernel": "hpsi_pass_kernel (all passes of one H.psi product), L=28 alpha=1.5 h=0.8",
@@ -798,6 +883,8 @@ def main():
         extra["trotter_nn_L24"] = trotter_nn()
     if rank == 0 and not args.no_rdm:
         extra["rdm_L24"] = rdm_L24()
+    if rank == 0 and not args.no_scale:
+        extra["scale_L30"] = scale_L30()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_line()
