@@ -53,7 +53,8 @@ def parse():
                     help="bond entropy per step: overlapped eigen-solve (async) or blocking (sync)")
     ap.add_argument("--main-priority", choices=["high", "default"], default="high",
                     help="priority of the stream the evolution runs on")
-    ap.add_argument("--profile-case", choices=["batch_L16", "gates_L24", "rdm_L24", "hpsi_L27", "quench_L24"],
+    ap.add_argument("--profile-case", choices=["batch_L16", "gates_L24", "rdm_L24", "hpsi_L27", "quench_L24",
+                                               "hpsi_fp64_L24", "krylov_L24"],
                     default=None,
                     help="run one small profiling workload and exit (for ncu captures)")
     return ap.parse_args()
@@ -786,6 +787,31 @@ def profile_case(name):
         c.apply_H(y, x)
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": name, "norm": float(torch.linalg.vector_norm(x).item())}))
+        c.close()
+    elif name == "hpsi_fp64_L24":
+        # complex128 H.psi at L = 24 (alpha = 1.5, h = 0.8): one product with the flip sums on
+        # FP32 pairs, one with FP64 multiply-adds (three passes each)
+        from paper_1802_10052_gb300 import Chain
+        L = 24
+        c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="fp64")
+        x = torch.from_numpy(si.gaussian_state(L, 24)).cuda()
+        y = c.new_state()
+        for mode in (1, 0):
+            c.set_flip_sums(mode)
+            c.apply_H(x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "norm": float(torch.linalg.vector_norm(y).item())}))
+        c.close()
+    elif name == "krylov_L24":
+        # one Krylov step (m = 20) of the L = 24 quench state at t = 0.1, complex64: 20 products
+        # with the Krylov epilogue, as in the benchmark step
+        from paper_1802_10052_gb300 import Chain
+        c = Chain(WL["L"], J=WL["J"], alpha=WL["alpha"], h=WL["h"], prec="mixed")
+        x = c.new_state()
+        c.init_basis_state(x, 0)
+        c.krylov_evolve(x, WL["dt"], 11, WL["m"])
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name}))
         c.close()
     elif name == "quench_L24":
         # the benchmark workload (10 Krylov steps, <sz>, <szsz>, S per step), complex64: five

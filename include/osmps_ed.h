@@ -154,6 +154,18 @@ osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);
  * 0 <= tiles <= 4.  Not from the paper (memory scheduling). */
 osmps_status osmps_ed_set_prefetch(osmps_ed_t *ed, int tiles);
 
+/* Arithmetic of the sigma^x flip sums of complex128 H.psi (not from the paper;
+ * numerics).  1 (the default): in every pass whose flipped bits share one field
+ * value, each amplitude is split once into FP32 hi and lo parts (exact to 2^-48
+ * relative, by integer operations) and the flipped partners are summed on the
+ * FP32 pipes with the exact rounding error of every addition kept (TwoSum),
+ * then multiplied by the field in FP64; the FP64 pipe,
+ * ~58x slower than the FP32 pipes on this part, keeps only the field, the
+ * diagonal, the stream and the epilogue.  Amplitudes below 2^-126 in magnitude
+ * count as zero.  0: FP64 multiply-adds for every flip.  No effect on complex64
+ * handles.  Takes effect at the next product. */
+osmps_status osmps_ed_set_flip_sums(osmps_ed_t *ed, int mode);
+
 /* D = 2^L. */
 osmps_status osmps_ed_dim(const osmps_ed_t *ed, uint64_t *D);
 

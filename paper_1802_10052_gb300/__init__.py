@@ -270,6 +270,10 @@ class Chain:
         quotients of the Gram product's eigenvectors (complex64); 3: automatic (default)."""
         check(lib.osmps_ed_set_entropy_method(self._h, int(method)), "osmps_ed_set_entropy_method")
 
+    def set_flip_sums(self, mode):
+        """complex128 flip sums: 1 = FP32 pairs with exact error terms where the field is uniform (default), 0 = FP64."""
+        check(lib.osmps_ed_set_flip_sums(self._h, int(mode)), "osmps_ed_set_flip_sums")
+
     def set_prefetch(self, tiles):
         """L2 prefetch distance of the H.psi passes (tiles ahead; 0 = off)."""
         check(lib.osmps_ed_set_prefetch(self._h, int(tiles)), "osmps_ed_set_prefetch")

@@ -681,6 +681,7 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
     for (int b = 0; b < L; ++b) hd->hbit[b] = h;
     hd->reorth = 0;
     hd->entropy_method = ENT_AUTO;
+    hd->flip_pairs = 1;
     hd->prefetch = (prec == OSMPS_FP64) ? 0 : 1;  // FP64 passes are bound by the FP64 pipe, not by latency
     cudaError_t err = cudaGetDevice(&hd->device);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&hd->nsm, cudaDevAttrMultiProcessorCount, hd->device);
@@ -781,6 +782,12 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm) {
 osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method) {
     if (ed == nullptr || method < ENT_GRAM || method > ENT_AUTO) return OSMPS_EINVAL;
     ed->h.entropy_method = method;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_flip_sums(osmps_ed_t *ed, int mode) {
+    if (ed == nullptr || (mode != 0 && mode != 1)) return OSMPS_EINVAL;
+    ed->h.flip_pairs = mode;
     return OSMPS_OK;
 }
 

@@ -60,8 +60,67 @@ struct PassParams {
     int L, c, o, g, ta, first, last, epilogue, rank;
     int pf;                             // L2 prefetch distance in tiles beyond the shared-memory stages
     unsigned tile_bytes;
+    int df;                             // complex128 with one field on every flipped bit: flip sums on FP32 pairs
+    double dfh;                         // that field
     T hb[kMaxL + 1];
 };
+
+// ---- complex128 flip sums on the FP32 pipes ----
+// x = hi + lo exactly up to 2^-48 |x| with hi, lo FP32 (hi: the top 24 bits of
+// the mantissa, lo: the next 24 of the remaining 29), by integer operations
+// only; |x| below 2^-126 is flushed to zero (an absolute error < 1.2e-38).
+__device__ __forceinline__ void split_df(double x, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const int e32 = e - 1023 + 127;
+    if (e32 <= 0) {
+        hi = 0.0f;
+        lo = 0.0f;
+        return;
+    }
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    hi = __uint_as_float(sign | ((unsigned)(e32 < 255 ? e32 : 255) << 23) | (unsigned)(m >> 29));
+    const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);  // x - hi = rem 2^(e - 1075)
+    if (rem == 0u) {
+        lo = 0.0f;
+        return;
+    }
+    const int pl = 31 - __clz(rem);  // leading one of rem
+    const int le = pl + e - 1075 + 127;
+    if (le <= 0) {
+        lo = 0.0f;
+        return;
+    }
+    const unsigned mant = pl >= 23 ? (rem >> (pl - 23)) : (rem << (23 - pl));
+    lo = __uint_as_float(sign | ((unsigned)le << 23) | (mant & 0x7FFFFFu));
+}
+// exact FP32 -> FP64 by integer operations (FP32 denormals flushed to zero)
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    if (e == 0u) return 0.0;
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)d);
+}
+// Sum of the hi parts with the exact rounding error of every addition (Knuth's
+// TwoSum, no condition on the order of magnitudes) accumulated beside it (the
+// cascaded summation of Ogita, Rump and Oishi 2005), plain FP32 sum of the lo
+// parts: error O((n u)^2) of the sum of magnitudes, u = 2^-24.
+struct DfAcc {
+    float s, c, l;
+};
+__device__ __forceinline__ void df_add(DfAcc &a, float hi, float lo) {
+    const float t = a.s + hi;
+    const float bp = t - a.s;
+    const float ap = t - bp;
+    a.c += (a.s - ap) + (hi - bp);
+    a.s = t;
+    a.l += lo;
+}
+__device__ __forceinline__ double df_value(const DfAcc &a) { return f2d_bits(a.s) + (f2d_bits(a.c) + f2d_bits(a.l)); }
 
 __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *tm, int rank, const int *crd,
                                          unsigned long long *bar) {
@@ -162,6 +221,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     const int oc = p.o - p.c;
     const uint64_t ocmask = (1ull << oc) - 1ull;
     const bool has_stream = p.stream != nullptr;
+    const bool dfm = (sizeof(T) == sizeof(double)) && p.df != 0;  // FP32-pair flip sums
 
     auto coords = [&](long long t, int *crd) {
         if (p.rank == 3) {
@@ -260,7 +320,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             if (!ok) {
                 if (lane == 0) atomicExch(p.err, 1);
                 failed = true;
-                break;
+                if (!dfm) break;  // FP32-pair mode: every thread leaves together at the tile barrier
             }
         }
         if (warp == 0 && lane == 0 && p.pf > 0) {
@@ -297,9 +357,18 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         const T *tcur = tab + s * kTab;
         const uint64_t tt = (uint64_t)t;
         const uint64_t base = ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
-        if (!mbar_wait(&fullU[s], (unsigned)((n / kStages) & 1), p.err)) {
-            atomicExch(p.err, 1);
-            break;
+        {
+            const bool okw = mbar_wait(&fullU[s], (unsigned)((n / kStages) & 1), p.err);
+            if (dfm) {
+                if (__syncthreads_or(!okw || failed)) {
+                    atomicExch(p.err, 1);
+                    failed = true;
+                    break;
+                }
+            } else if (!okw) {
+                atomicExch(p.err, 1);
+                break;
+            }
         }
         const T *trow = tcur;
         T pd0 = 0, pd1 = 0, pn = 0;
@@ -310,6 +379,24 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             if (full_tile || i < nmine) unpackv(Ucur[i * kPassThreads + tid], &self[i * VE]);
             else unpackv(V{}, &self[i * VE]);
         }
+        if constexpr (sizeof(T) == sizeof(double)) {
+            if (dfm) {
+                // this thread's amplitudes to (re_hi, re_lo, im_hi, im_lo) in place; the
+                // flips below read every partner in that form
+                float4 *Uf = reinterpret_cast<float4 *>(const_cast<V *>(Ucur));
+#pragma unroll
+                for (int i = 0; i < kBV; ++i) {
+                    if (full_tile || i < nmine) {
+                        const double2 a = self[i];
+                        float4 f;
+                        split_df(a.x, f.x, f.y);
+                        split_df(a.y, f.z, f.w);
+                        Uf[i * kPassThreads + tid] = f;
+                    }
+                }
+                __syncthreads();
+            }
+        }
         // accumulate in two halves of eight vectors; all four bits of i are
         // flipped in registers
 #pragma unroll
@@ -318,7 +405,33 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             A r[NH * VE];
 #pragma unroll
             for (int e = 0; e < NH * VE; ++e) r[e] = azero(T(0));
-            if (VE == 2 && p.c == 0) {
+            if constexpr (sizeof(T) == sizeof(double)) {
+                if (dfm) {
+                    // complex128, one field on every flipped bit: sum of the flipped
+                    // partners on FP32 pairs with exact error terms, then one FP64 multiply
+                    const float4 *Uf = reinterpret_cast<const float4 *>(Ucur);
+                    DfAcc ar[NH], ai[NH];
+#pragma unroll
+                    for (int i = 0; i < NH; ++i) ar[i] = ai[i] = DfAcc{0.0f, 0.0f, 0.0f};
+                    for (int lb = p.c; lb < tbits; ++lb) {
+#pragma unroll
+                        for (int i = 0; i < NH; ++i) {
+                            const int ii = hh * NH + i;
+                            if (full_tile || ii < nmine) {
+                                const float4 v = Uf[(ii * kPassThreads + tid) ^ (1 << lb)];
+                                df_add(ar[i], v.x, v.y);
+                                df_add(ai[i], v.z, v.w);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < NH; ++i) {
+                        r[i].x = p.dfh * df_value(ar[i]);
+                        r[i].y = p.dfh * df_value(ai[i]);
+                    }
+                }
+            }
+            if (!dfm && VE == 2 && p.c == 0) {
                 // bit 0 lives inside the 16-byte vector
                 const K f = mkcoef(p.hb[p.o]);
 #pragma unroll
@@ -331,7 +444,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
 #pragma unroll
             for (int j = 0; j < kIBits; ++j) {
                 const int lb = LOGVE + kTBits + j;  // local bit carried by bit j of i
-                if (lb >= p.c && lb < tbits) {
+                if (!dfm && lb >= p.c && lb < tbits) {
                     const K f = mkcoef(p.hb[p.o + lb - p.c]);
 #pragma unroll
                     for (int i = 0; i < NH; ++i) {
@@ -342,7 +455,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
             // flips of the eight bits of tid: neighbour vectors from shared memory
-            {
+            if (!dfm) {
                 const int lb0 = p.c > LOGVE ? p.c : LOGVE;
                 const int lb1 = tbits < LOGVE + kTBits ? tbits : LOGVE + kTBits;
                 for (int lb = lb0; lb < lb1; ++lb) {
@@ -385,7 +498,9 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
             if (hh == 1) {
-                // u stage s is no longer read by this warp
+                // u stage s is no longer read by this warp (its FP32-pair stores
+                // are ordered before the next bulk copy into the stage)
+                if (dfm) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&emptyU[s]);
             }
@@ -394,7 +509,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                     if (!mbar_wait(fullS, (unsigned)(n & 1), p.err)) {
                         atomicExch(p.err, 1);
                         failed = true;
-                        break;
+                        if (!dfm) break;  // FP32-pair mode: leave at the next tile barrier
                     }
                     stream_ready = true;
                 }
@@ -447,7 +562,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
         }
-        if (failed) break;
+        if (failed && !dfm) break;
         acc_d0 += (double)pd0;
         acc_d1 += (double)pd1;
         acc_n += (double)pn;
@@ -775,6 +890,17 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.pf = h->prefetch;
         p.tile_bytes = (unsigned)((1u << (d.c + d.g)) * h->esize);
         for (int k = 0; k <= kMaxL; ++k) p.hb[k] = (T)h->hbit[k];
+        // complex128 passes whose flipped bits share one field sum on FP32 pairs
+        p.df = 0;
+        p.dfh = 0.0;
+        if (sizeof(T) == sizeof(double) && h->flip_pairs) {
+            bool uniform = true;
+            for (int k = d.o + 1; k < d.o + d.g; ++k) uniform = uniform && (h->hbit[k] == h->hbit[d.o]);
+            if (uniform) {
+                p.df = 1;
+                p.dfh = h->hbit[d.o];
+            }
+        }
         const int grid = grid_for<T>(h, d.ntiles);
         hpsi_pass_kernel<T><<<grid, kHpsiThreads, pass_smem(), h->stream>>>(tm_u, tm_s, p);
         h->launches += 1;

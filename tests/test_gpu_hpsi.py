@@ -127,3 +127,45 @@ def test_prefetch_and_sm_count_do_not_change_the_product(L, prec):
         c.apply_H(x, out)
         assert torch.equal(out, ref), (pf, nsm)
     c.close()
+
+
+@pytest.mark.parametrize("L", [3, 8, 12, 13, 14, 18, 20])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp64_flip_sums_match_csr(L, mode):
+    """complex128 H.psi with the flip sums on FP32 pairs with exact error terms (mode 1, used
+    where every flipped bit of a pass has the same field) and on FP64 multiply-adds
+    (mode 0), uniform and site-dependent fields, against the CSR product."""
+    from paper_1802_10052_gb300 import Chain
+    rng = np.random.default_rng(500 + L)
+    Jr = rng.normal(size=L - 1)
+    psi = si.gaussian_state(L, 7 + L)
+    x = to_dev(psi, "fp64")
+    for hk in ([0.83] * L, list(rng.normal(size=L))):
+        c = chain_for(L, Jr, hk, "fp64")
+        c.set_flip_sums(mode)
+        out = c.new_state()
+        c.apply_H(x, out)
+        ref = O.hamiltonian_csr(L, Jr, hk) @ psi
+        got = to_host(out)
+        assert rel(got, ref) < 1e-13
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)) * 10)
+        c.close()
+
+
+def test_fp64_flip_sums_wide_dynamic_range():
+    """Amplitudes spread over sixty decades (1e-30 .. 1): every output element,
+    small ones included, to 1e-12 of its own size plus 1e-30 of the largest."""
+    L = 14
+    rng = np.random.default_rng(77)
+    psi = si.gaussian_state(L, 77) * 10.0 ** rng.uniform(-30, 0, size=1 << L)
+    Jr = O.coupling_table(L, 1.0, 1.5)
+    ref = O.RuleSetH(L, Jr, 0.8)(psi)
+    from paper_1802_10052_gb300 import Chain
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="fp64")
+    x = to_dev(psi, "fp64")
+    out = c.new_state()
+    c.apply_H(x, out)
+    got = to_host(out)
+    bound = np.abs(O.RuleSetH(L, np.abs(Jr), 0.8)(np.abs(psi))) + np.abs(O.diagonal_energy(L, Jr, np.arange(1 << L)) * psi)
+    assert np.all(np.abs(got - ref) <= 1e-12 * bound + 1e-30 * np.max(np.abs(psi)))
+    c.close()

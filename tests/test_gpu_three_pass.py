@@ -97,3 +97,18 @@ def test_krylov_L27_lrqi_quench_mixed_against_fp64():
     e0 = sum((L - r) / r ** 1.5 for r in range(1, L))
     assert abs(nf - 1.0) < 1e-12 and abs(ef / nf - e0) < TOL["fp64"] * abs(e0)
     assert abs(em / nm - e0) < TOL["mixed"] * abs(e0)
+
+
+@pytest.mark.timeout(900)
+@pytest.mark.parametrize("Lc,prec,tol", [(26, "mixed", 1e-6), (24, "fp64", 1e-10)])
+def test_lanczos_three_pass_nn_chain_jordan_wigner(Lc, prec, tol):
+    """Ground energy of the open nearest-neighbour chain (J = 1, h = 2, gapped) on the
+    three-pass layout (complex64 from L = 26, complex128 from L = 24) against the
+    Jordan-Wigner closed form, which holds at any L."""
+    c = Chain(Lc, couplings=[1.0] + [0.0] * (Lc - 2), h=2.0, prec=prec)
+    c.set_reorth(0)
+    x = seeded_device_state(Lc, 2600 + Lc, prec)
+    E, res, it = c.lanczos_ground(x, tol=tol, max_iter=120, raise_on_noconv=(prec == "fp64"))
+    want = O.jordan_wigner_ground_energy(Lc, 1.0, 2.0)
+    assert abs(E - want) < TOL[prec] * abs(want), (E, want, res, it)
+    c.close()
