@@ -155,15 +155,15 @@ osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);
 osmps_status osmps_ed_set_prefetch(osmps_ed_t *ed, int tiles);
 
 /* Arithmetic of the sigma^x flip sums of complex128 H.psi (not from the paper;
- * numerics).  1 (the default): in every pass whose flipped bits share one field
- * value, each amplitude is split once into FP32 hi and lo parts (exact to 2^-48
- * relative, by integer operations) and the flipped partners are summed on the
- * FP32 pipes with the exact rounding error of every addition kept (TwoSum),
- * then multiplied by the field in FP64; the FP64 pipe,
- * ~58x slower than the FP32 pipes on this part, keeps only the field, the
- * diagonal, the stream and the epilogue.  Amplitudes below 2^-126 in magnitude
- * count as zero.  0: FP64 multiply-adds for every flip.  No effect on complex64
- * handles.  Takes effect at the next product. */
+ * numerics).  1 (the default): in a pass that flips ten or more bits sharing one
+ * field value (the first pass), each amplitude is split once into FP32 hi and lo
+ * parts (exact to 2^-48 relative, by integer operations) and the flipped partners
+ * are summed on the FP32 pipes with the exact rounding error of every addition
+ * kept (TwoSum), then multiplied by the field in FP64; the rest of the product
+ * (and passes of fewer bits, where the split costs about as much as the FP64
+ * flips it replaces) uses FP64 multiply-adds.  Amplitudes below 2^-126 in
+ * magnitude count as zero in the split.  0: FP64 multiply-adds for every flip.
+ * No effect on complex64 handles.  Takes effect at the next product. */
 osmps_status osmps_ed_set_flip_sums(osmps_ed_t *ed, int mode);
 
 /* D = 2^L. */
@@ -246,9 +246,13 @@ osmps_status osmps_ed_krylov_evolve(osmps_ed_t *ed, void *psi, double dt, int ns
  *   h_steps     host array of nsteps fields.
  *   grad_h      host array of nsteps (may be NULL); grad_scale host (may be NULL).
  *   nquad       1..32 (8 resolves dt |H| up to ~3 to 1e-14).
- * Allocates (1 + nsteps/stride + stride + 5) state vectors and a second
- * Krylov workspace for the call, frees them before returning, and leaves the
- * handle's fields as they were.  Synchronises.
+ * Allocates (1 + nsteps/stride + stride + 5) state vectors, two more handles
+ * (a second Krylov workspace for the adjoint state, and the operator X alone),
+ * and, when they fit in a quarter of the free device memory, (stride - 1) * m
+ * more vectors that keep the Krylov bases built while a segment is recomputed
+ * (the backward sweep then does not rebuild them; same arithmetic, same
+ * results).  Everything is freed before returning; the handle's fields are
+ * left as they were.  Synchronises.
  */
 osmps_status osmps_ed_adjoint_grad(osmps_ed_t *ed, const void *psi0, int nsteps, double dt,
                                    const double *h_steps, int m, double h_target, int stride,

@@ -1232,6 +1232,31 @@ static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nste
         // <ls|X ps> and <ls|H_zz ps> of every node of every step, read back once at the end
         zd = static_cast<double *>(alloc(sizeof(double) * 4 * (size_t)nquad * nsteps));
     }
+    // Krylov bases of the segment's forward steps (the backward step k needs the basis of
+    // psi_{k-1} under H(h_k), which recomputing psi_k builds): kept when they fit in a quarter
+    // of the free device memory, else rebuilt in the backward sweep (same arithmetic, same bits)
+    std::vector<void *> bstore;
+    char *cstash = nullptr;
+    const size_t o_alpha = CTL_OFF(alpha), o_beta = CTL_OFF(beta), o_scale = CTL_OFF(scale), o_sc = CTL_OFF(nrm);
+    const size_t n_sc = CTL_OFF(m_eff) + sizeof(int) - o_sc;
+    const size_t cslot = sizeof(double) * (3 * (size_t)m + 2) + n_sc;  // alpha[m], beta[m+1], scale[m+1], scalars
+    if (want_grad && stride > 1 && st == OSMPS_OK) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        if ((size_t)(stride - 1) * m * vb <= fr / 4) {
+            bstore.assign((size_t)(stride - 1) * m, nullptr);
+            for (auto &b : bstore) b = alloc(vb);
+            cstash = static_cast<char *>(alloc(cslot * (size_t)(stride - 1)));
+            if (st != OSMPS_OK) {  // not enough after all: rebuild the bases instead
+                st = OSMPS_OK;
+                bstore.clear();
+                cstash = nullptr;
+            }
+        }
+    }
     osmps_ed_t *sib = nullptr;  // second handle: Krylov basis of the adjoint state
     osmps_ed_t *xop = nullptr;  // third handle: X = sum_k sigma^x_k alone (no couplings, unit field)
     auto cleanup = [&]() {
@@ -1317,9 +1342,30 @@ static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nste
         const int k0 = sgi * stride, k1 = std::min(nsteps, k0 + stride);
         // psi_{k0} .. psi_{k1-1} of this segment, recomputed from its checkpoint
         CKAC(cudaMemcpyAsync(seg[0], cp[sgi], vb, cudaMemcpyDeviceToDevice, h->stream));
+        const bool keep = !bstore.empty();
         for (int k = k0 + 1; k < k1; ++k) {
             CKAC(cudaMemcpyAsync(seg[k - k0], seg[k - k0 - 1], vb, cudaMemcpyDeviceToDevice, h->stream));
-            CKA(step(seg[k - k0], h_steps[k - 1]));
+            if (!keep) {
+                CKA(step(seg[k - k0], h_steps[k - 1]));
+            } else {
+                // the same step as its two halves (the kernels of osmps_ed_krylov_evolve in the
+                // same order), keeping the basis of psi_{k-1} and its scalars between them
+                set_h(h, h_steps[k - 1]);
+                CKA(krylov_basis(h, seg[k - k0], m));
+                const size_t slot = (size_t)(k - k0 - 1);
+                for (int i = 1; i <= m; ++i)
+                    CKAC(cudaMemcpyAsync(bstore[slot * m + i - 1], h->V[i], vb, cudaMemcpyDeviceToDevice, h->stream));
+                char *cs = cstash + slot * cslot;
+                char *cb = reinterpret_cast<char *>(h->ctl);
+                CKAC(cudaMemcpyAsync(cs, cb + o_alpha, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+                CKAC(cudaMemcpyAsync(cs + sizeof(double) * m, cb + o_beta, sizeof(double) * (m + 1),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+                CKAC(cudaMemcpyAsync(cs + sizeof(double) * (2 * m + 1), cb + o_scale, sizeof(double) * (m + 1),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+                CKAC(cudaMemcpyAsync(cs + sizeof(double) * (3 * m + 2), cb + o_sc, n_sc, cudaMemcpyDeviceToDevice,
+                                     h->stream));
+                CKA(krylov_combine(h, m, dt, seg[k - k0]));
+            }
         }
         for (int k = k1; k > k0; --k) {
             const double hk = h_steps[k - 1];
@@ -1327,7 +1373,25 @@ static osmps_status adjoint_grad_impl(osmps_ed_t *ed, const void *psi0, int nste
             // Krylov bases of psi_{k-1} (handle h) and lambda_k (handle hb) under H(h_k)
             set_h(h, hk);
             set_h(hb, hk);
-            CKA(krylov_basis(h, psi_prev, m));
+            if (keep && k < k1) {
+                // the basis kept from the recomputation of this segment
+                const size_t slot = (size_t)(k - k0 - 1);
+                CKA(ensure_basis(h, m));
+                for (int i = 1; i <= m; ++i)
+                    CKAC(cudaMemcpyAsync(h->V[i], bstore[slot * m + i - 1], vb, cudaMemcpyDeviceToDevice, h->stream));
+                CKA(upload_basis_table(h, psi_prev, m));
+                const char *cs = cstash + slot * cslot;
+                char *cb = reinterpret_cast<char *>(h->ctl);
+                CKAC(cudaMemcpyAsync(cb + o_alpha, cs, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+                CKAC(cudaMemcpyAsync(cb + o_beta, cs + sizeof(double) * m, sizeof(double) * (m + 1),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+                CKAC(cudaMemcpyAsync(cb + o_scale, cs + sizeof(double) * (2 * m + 1), sizeof(double) * (m + 1),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+                CKAC(cudaMemcpyAsync(cb + o_sc, cs + sizeof(double) * (3 * m + 2), n_sc, cudaMemcpyDeviceToDevice,
+                                     h->stream));
+            } else {
+                CKA(krylov_basis(h, psi_prev, m));
+            }
             CKA(krylov_basis(hb, lam, m));
             // Frechet derivative of exp(-i dt H) along X and along H_zz, by Gauss-Legendre in s:
             //   <lambda_k| L(A, E) psi_{k-1}> = int_0^1 <e^{i s dt H} lambda_k| E |e^{-i (1-s) dt H} psi_{k-1}> ds

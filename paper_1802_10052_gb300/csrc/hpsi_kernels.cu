@@ -890,10 +890,13 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.pf = h->prefetch;
         p.tile_bytes = (unsigned)((1u << (d.c + d.g)) * h->esize);
         for (int k = 0; k <= kMaxL; ++k) p.hb[k] = (T)h->hbit[k];
-        // complex128 passes whose flipped bits share one field sum on FP32 pairs
+        // complex128 passes that flip many bits sharing one field sum on FP32 pairs:
+        // the split and recombination cost about as much as six FP64 flips, and
+        // the FP32-pair code is issue-bound at this kernel's 8 warps per SM, so
+        // only the passes of ten or more flipped bits (the first) gain
         p.df = 0;
         p.dfh = 0.0;
-        if (sizeof(T) == sizeof(double) && h->flip_pairs) {
+        if (sizeof(T) == sizeof(double) && h->flip_pairs && d.g >= 10) {
             bool uniform = true;
             for (int k = d.o + 1; k < d.o + d.g; ++k) uniform = uniform && (h->hbit[k] == h->hbit[d.o]);
             if (uniform) {

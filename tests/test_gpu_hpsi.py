@@ -133,7 +133,7 @@ def test_prefetch_and_sm_count_do_not_change_the_product(L, prec):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_fp64_flip_sums_match_csr(L, mode):
     """complex128 H.psi with the flip sums on FP32 pairs with exact error terms (mode 1, used
-    where every flipped bit of a pass has the same field) and on FP64 multiply-adds
+    in passes of ten or more flipped bits that share one field) and on FP64 multiply-adds
     (mode 0), uniform and site-dependent fields, against the CSR product."""
     from paper_1802_10052_gb300 import Chain
     rng = np.random.default_rng(500 + L)
