@@ -789,8 +789,8 @@ def profile_case(name):
         print(json.dumps({"profile_case": name, "norm": float(torch.linalg.vector_norm(x).item())}))
         c.close()
     elif name == "hpsi_fp64_L24":
-        # complex128 H.psi at L = 24 (alpha = 1.5, h = 0.8): one product with the flip sums on
-        # FP32 pairs, one with FP64 multiply-adds (three passes each)
+        # complex128 H.psi at L = 24 (alpha = 1.5, h = 0.8): one product with the flip sums in
+        # 64-bit fixed point, one with FP64 multiply-adds (three passes each)
         from paper_1802_10052_gb300 import Chain
         L = 24
         c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="fp64")

@@ -139,8 +139,9 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm);
  *      in FP32, so S keeps ~1e-7 in complex64 at ~1.1x the cost of 0; values
  *      of nearly equal size (closer than ~1e-7) come out as averages of each
  *      other, which moves S only at second order.  Scratch (4 n^2 + 2 n K complex-sized floats) is kept by the handle.
- *      Falls back to 1 when the library eigen-solver fails.  EUNSUPPORTED
- *      where it does not apply.
+ *      Falls back to 1 when the library eigen-solver fails or its eigenvectors
+ *      give a non-finite value (seen for nearly product states whose rho has
+ *      FP32-subnormal entries).  EUNSUPPORTED where it does not apply.
  *   3  automatic (the default): complex128 takes 0 (FP64 Gram and eigenvalues
  *      meet 1e-10); complex64 takes 2 where it applies, else 1 for blocks up
  *      to 8192 rows, else 0.
@@ -154,16 +155,27 @@ osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);
  * 0 <= tiles <= 4.  Not from the paper (memory scheduling). */
 osmps_status osmps_ed_set_prefetch(osmps_ed_t *ed, int tiles);
 
+/* CTA shape of the H.psi passes (not from the paper; scheduling): 256 threads
+ * holding 16 vectors of a 64 KiB tile each, or 512 threads holding 8 (twice the
+ * warps per SM to hide latency, one more bit flipped through shared memory).
+ * Defaults: 256 for OSMPS_MIXED (its passes are issue-bound and the 128-register
+ * cap of the larger CTA adds instructions), 512 for OSMPS_FP64 (latency-bound,
+ * 3 % faster).  Results agree to rounding (the order of the flip terms
+ * differs).  Takes effect at the next product. */
+osmps_status osmps_ed_set_pass_threads(osmps_ed_t *ed, int threads);
+
 /* Arithmetic of the sigma^x flip sums of complex128 H.psi (not from the paper;
- * numerics).  1 (the default): in a pass that flips ten or more bits sharing one
- * field value (the first pass), each amplitude is split once into FP32 hi and lo
- * parts (exact to 2^-48 relative, by integer operations) and the flipped partners
- * are summed on the FP32 pipes with the exact rounding error of every addition
- * kept (TwoSum), then multiplied by the field in FP64; the rest of the product
- * (and passes of fewer bits, where the split costs about as much as the FP64
- * flips it replaces) uses FP64 multiply-adds.  Amplitudes below 2^-126 in
- * magnitude count as zero in the split.  0: FP64 multiply-adds for every flip.
- * No effect on complex64 handles.  Takes effect at the next product. */
+ * numerics).  mode >= 1 (default 1): in every pass that flips at least `mode`
+ * bits sharing one field value, the tile's amplitudes are put on one 64-bit
+ * fixed-point grid (unit 2^-57 of the tile's largest magnitude or finer;
+ * truncation toward zero, by integer operations), the flipped partners are
+ * summed exactly in integers and the sum is rounded back to FP64 and multiplied
+ * by the field.  Each sum is thus within (number of flipped bits) units of the
+ * exact one: relative to the largest amplitude of the tile, not to the partners'
+ * own magnitudes.  A non-finite amplitude makes its tile's sums NaN.  Passes with
+ * site-dependent fields, and every pass with mode 0, use FP64 multiply-adds.
+ * 0 <= mode <= 30.  No effect on complex64 handles.  Takes effect at the next
+ * product. */
 osmps_status osmps_ed_set_flip_sums(osmps_ed_t *ed, int mode);
 
 /* D = 2^L. */

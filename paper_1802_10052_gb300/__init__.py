@@ -271,8 +271,13 @@ class Chain:
         check(lib.osmps_ed_set_entropy_method(self._h, int(method)), "osmps_ed_set_entropy_method")
 
     def set_flip_sums(self, mode):
-        """complex128 flip sums: 1 = FP32 pairs with exact error terms where the field is uniform (default), 0 = FP64."""
+        """complex128 flip sums: k >= 1 = exact 64-bit fixed-point sums in uniform-field passes
+        flipping at least k bits (default 1), 0 = FP64 multiply-adds."""
         check(lib.osmps_ed_set_flip_sums(self._h, int(mode)), "osmps_ed_set_flip_sums")
+
+    def set_pass_threads(self, threads):
+        """CTA shape of the H.psi passes: 256 (16 vectors per thread) or 512 (8)."""
+        check(lib.osmps_ed_set_pass_threads(self._h, int(threads)), "osmps_ed_set_pass_threads")
 
     def set_prefetch(self, tiles):
         """L2 prefetch distance of the H.psi passes (tiles ahead; 0 = off)."""

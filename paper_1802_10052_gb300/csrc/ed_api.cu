@@ -681,7 +681,8 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
     for (int b = 0; b < L; ++b) hd->hbit[b] = h;
     hd->reorth = 0;
     hd->entropy_method = ENT_AUTO;
-    hd->flip_pairs = 1;
+    hd->flip_fixed = 1;
+    hd->pass_threads = 512;
     hd->prefetch = (prec == OSMPS_FP64) ? 0 : 1;  // FP64 passes are bound by the FP64 pipe, not by latency
     cudaError_t err = cudaGetDevice(&hd->device);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&hd->nsm, cudaDevAttrMultiProcessorCount, hd->device);
@@ -786,8 +787,14 @@ osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method) {
 }
 
 osmps_status osmps_ed_set_flip_sums(osmps_ed_t *ed, int mode) {
-    if (ed == nullptr || (mode != 0 && mode != 1)) return OSMPS_EINVAL;
-    ed->h.flip_pairs = mode;
+    if (ed == nullptr || mode < 0 || mode > kMaxL) return OSMPS_EINVAL;
+    ed->h.flip_fixed = mode;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_pass_threads(osmps_ed_t *ed, int threads) {
+    if (ed == nullptr || (threads != 256 && threads != 512)) return OSMPS_EINVAL;
+    ed->h.pass_threads = threads;
     return OSMPS_OK;
 }
 
@@ -1043,18 +1050,23 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
             h->lam_cap = n + 1;
         }
         const osmps_status rs = schmidt_rayleigh(h, psi, cut, h->gram, h->lam_dev, h->lam_dev + n);
-        if (rs == OSMPS_ENOCONV)
+        if (rs == OSMPS_ENOCONV) {
             method = ENT_SVD;  // the library eigen-solver failed: singular values of M instead
-        else if (rs != OSMPS_OK)
+        } else if (rs != OSMPS_OK) {
             return rs;
-        else {
-            if (lambda)
-                CK(cudaMemcpyAsync(lambda, h->lam_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+        } else {
             double Sv = 0.0;
             CK(cudaMemcpyAsync(&Sv, h->lam_dev + n, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
-            if (S) *S = Sv;
-            return OSMPS_OK;
+            if (std::isfinite(Sv)) {
+                if (lambda) {
+                    CK(cudaMemcpyAsync(lambda, h->lam_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+                    CK(cudaStreamSynchronize(h->stream));
+                }
+                if (S) *S = Sv;
+                return OSMPS_OK;
+            }
+            method = ENT_SVD;  // non-finite eigenvectors from the library: singular values of M instead
         }
     }
     if (method == ENT_SVD) {

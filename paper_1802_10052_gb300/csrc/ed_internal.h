@@ -203,7 +203,8 @@ struct Handle {
     size_t gram_aux_bytes;
     int gram_mode;              // 0 automatic, 1 CUDA cores, 2 tensor cores
     int prefetch;               // L2 prefetch distance of the H.psi passes (tiles)
-    int flip_pairs;             // complex128: flip sums of uniform-field passes on FP32 pairs
+    int pass_threads;           // H.psi CTA shape: 256 (16 vectors per thread) or 512 (8)
+    int flip_fixed;             // complex128: fewest flipped bits of a uniform-field pass summed in fixed point (0 = none)
     int entropy_method;         // EntropyMethod
     void *solver_ws;            // cuSOLVER workspace
     size_t solver_ws_bytes;

@@ -23,8 +23,8 @@
 //   half), so each amplitude costs three lookups and two adds.
 // * The last pass optionally fuses the Lanczos/Krylov epilogue
 //       w = sv*H u - a*sv*u - b*uprev
-//   and the inner products <sv u, w> and |w|^2 (FP32 per thread and tile,
-//   FP64 across tiles and CTAs, fixed reduction order).
+//   and the inner products <sv u, w> and |w|^2 (FP32 per thread, tile and
+//   warp, FP64 across tiles and CTAs, fixed reduction order).
 #include <cuda.h>  // CUtensorMap types; the encoder is fetched through the runtime's driver entry point
 #include <cuda_runtime.h>
 
@@ -33,17 +33,16 @@
 
 namespace osmps {
 
-constexpr int kBV = 16;                                 // 16-byte vectors per consumer thread per tile
-constexpr int kHB = kBV / 2;                            // processed in two halves
 constexpr int kTileV = 1 << (kTileBytesLog2 - 4);       // 16-byte vectors per tile
 constexpr int kTab = 192;                               // TA (<= 64) + TB (<= 128) per stage
 constexpr int kStages = 2;                              // shared-memory ring of u tiles
-constexpr int kConsumerWarps = kPassThreads / 32;       // 8
-constexpr int kIBits = 4;                               // log2 kBV: vector-index bits held in registers
-constexpr int kTBits = 8;                               // log2 kPassThreads
-constexpr int kHpsiThreads = kPassThreads;              // warp 0 also issues the copies
-static_assert(kTileV == kBV * kPassThreads && (1 << kIBits) == kBV && (1 << kTBits) == kPassThreads,
-              "sixteen vectors per consumer thread per tile");
+constexpr int kMaxPassWarps = kTileV / 8 / 32;          // 16: the 512-thread shape
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+// Two CTA shapes over the same 64 KiB tile: BV = 16 vectors per thread (256
+// threads: four vector-index bits flipped in registers, eight thread bits from
+// shared memory) or BV = 8 (512 threads: three in registers, nine from shared
+// memory, twice the warps to hide latency with half the registers).
+static_assert(kTileV / 16 == kPassThreads, "the 256-thread shape holds sixteen vectors per thread");
 
 template <typename T>
 struct PassParams {
@@ -60,67 +59,41 @@ struct PassParams {
     int L, c, o, g, ta, first, last, epilogue, rank;
     int pf;                             // L2 prefetch distance in tiles beyond the shared-memory stages
     unsigned tile_bytes;
-    int df;                             // complex128 with one field on every flipped bit: flip sums on FP32 pairs
-    double dfh;                         // that field
+    int fx;                             // complex128 with one field on every flipped bit: flip sums in fixed point
+    double fxh;                         // that field
     T hb[kMaxL + 1];
 };
 
-// ---- complex128 flip sums on the FP32 pipes ----
-// x = hi + lo exactly up to 2^-48 |x| with hi, lo FP32 (hi: the top 24 bits of
-// the mantissa, lo: the next 24 of the remaining 29), by integer operations
-// only; |x| below 2^-126 is flushed to zero (an absolute error < 1.2e-38).
-__device__ __forceinline__ void split_df(double x, float &hi, float &lo) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7ffull);
-    const int e32 = e - 1023 + 127;
-    if (e32 <= 0) {
-        hi = 0.0f;
-        lo = 0.0f;
-        return;
-    }
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    hi = __uint_as_float(sign | ((unsigned)(e32 < 255 ? e32 : 255) << 23) | (unsigned)(m >> 29));
-    const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);  // x - hi = rem 2^(e - 1075)
-    if (rem == 0u) {
-        lo = 0.0f;
-        return;
-    }
-    const int pl = 31 - __clz(rem);  // leading one of rem
-    const int le = pl + e - 1075 + 127;
-    if (le <= 0) {
-        lo = 0.0f;
-        return;
-    }
-    const unsigned mant = pl >= 23 ? (rem >> (pl - 23)) : (rem << (23 - pl));
-    lo = __uint_as_float(sign | ((unsigned)le << 23) | (mant & 0x7FFFFFu));
+// ---- complex128 flip sums in 64-bit fixed point ----
+// All amplitudes of a tile go on one grid of unit 2^(et - 1080), et the largest
+// biased FP64 exponent in the tile, so every |X| < 2^58 and the sum of a
+// partner per flipped bit (at most 12) is exact in 64-bit integers.  Onto the
+// grid by integer operations; back by one conversion, the unit folded into the
+// field: the FP64 pipe (2 lanes per clock per SM on this part) is left to the
+// diagonal, the partial sum and the epilogue.
+__device__ __forceinline__ unsigned fx_expo(double x) {
+    return (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu;
 }
-// exact FP32 -> FP64 by integer operations (FP32 denormals flushed to zero)
-__device__ __forceinline__ double f2d_bits(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xFFu;
-    if (e == 0u) return 0.0;
-    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
-                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)d);
+// x on the grid, truncated toward zero (error below one unit, i.e. below
+// 2^-57 of the tile's largest magnitude); zero and subnormals give 0
+__device__ __forceinline__ long long fx_from(double x, int et) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(((unsigned long long)b >> 52) & 0x7FFull);
+    const unsigned long long M = (((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << 5;
+    const int sh = et - e;  // >= 0
+    unsigned long long a = sh < 64 ? (M >> sh) : 0ull;
+    if (e == 0) a = 0ull;
+    const long long sg = b >> 63;  // 0 or -1
+    return ((long long)a ^ sg) - sg;
 }
-// Sum of the hi parts with the exact rounding error of every addition (Knuth's
-// TwoSum, no condition on the order of magnitudes) accumulated beside it (the
-// cascaded summation of Ogita, Rump and Oishi 2005), plain FP32 sum of the lo
-// parts: error O((n u)^2) of the sum of magnitudes, u = 2^-24.
-struct DfAcc {
-    float s, c, l;
-};
-__device__ __forceinline__ void df_add(DfAcc &a, float hi, float lo) {
-    const float t = a.s + hi;
-    const float bp = t - a.s;
-    const float ap = t - bp;
-    a.c += (a.s - ap) + (hi - bp);
-    a.s = t;
-    a.l += lo;
+// the field times the grid unit: one FP64 multiply per value turns an integer
+// sum (converted with rounding to nearest) into its term; tiles whose largest
+// magnitude is under 2^-960 get 0, a non-finite amplitude in the tile NaN
+__device__ __forceinline__ double fx_scale(double h, int et) {
+    if (et >= 2047) return __longlong_as_double(0x7FF8000000000000ll);
+    if (et <= 57) return 0.0;
+    return h * __longlong_as_double((long long)(et - 57) << 52);
 }
-__device__ __forceinline__ double df_value(const DfAcc &a) { return f2d_bits(a.s) + (f2d_bits(a.c) + f2d_bits(a.l)); }
 
 __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *tm, int rank, const int *crd,
                                          unsigned long long *bar) {
@@ -175,17 +148,22 @@ __device__ __forceinline__ double ld_keep(const double *ptr) {
 //    the first pass, partial sum later), all by TMA (cp.async.bulk.tensor,
 //    completion on mbarriers), as soon as the stage is released, and builds
 //    the first pass's per-tile diagonal tables;
-//  * all 8 warps own the vectors q = tid + 256 i (i < 16) of a
-//    tile: flips of the amplitude bit inside a vector and of the four bits of
-//    i are formed in registers, flips of the eight bits of tid from shared
-//    memory; the stream is read from its stage; results go to global memory
-//    with lane-coalesced stores.
+//  * all warps own the vectors q = tid + NT i (i < BV) of a tile: flips of
+//    the amplitude bit inside a vector and of the bits of i are formed in
+//    registers, flips of the bits of tid from shared memory; the stream is
+//    read from its stage; results go to global memory with lane-coalesced
+//    stores.
 // All waits are bounded (2 s); on timeout the error flag is raised, warp 0
 // waits for the copies it issued, and the kernel returns.
-template <typename T>
-__global__ void __launch_bounds__(kHpsiThreads, 1)
+template <typename T, int BV>
+__global__ void __launch_bounds__(kTileV / BV, 1)
     hpsi_pass_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_s,
                      PassParams<T> p) {
+    constexpr int NT = kTileV / BV;      // threads; all of them consume, warp 0 also issues the copies
+    constexpr int NW = NT / 32;          // consumer warps
+    constexpr int IBITS = ilog2c(BV);    // vector-index bits held in registers
+    constexpr int TBITS = ilog2c(NT);    // thread bits, flipped through shared memory
+    constexpr int HB = BV / 2;           // vectors per batch of shared-memory loads
     typedef typename Cx<T>::v16 V;
     typedef typename Cx<T>::amp A;
     typedef typename Cx<T>::coef K;
@@ -200,6 +178,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     unsigned long long *emptyU = fullU + kStages;
     unsigned long long *fullS = emptyU + kStages;
     unsigned long long *emptyS = fullS + 1;
+    unsigned *fxe = reinterpret_cast<unsigned *>(emptyS + 1);  // per stage: the tile's largest FP64 exponent
 
     if (p.m_eff != nullptr && *p.m_eff <= p.stop_index) return;
 
@@ -207,10 +186,11 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&fullU[s], 1);
-            mbar_init(&emptyU[s], kConsumerWarps);
+            mbar_init(&emptyU[s], NW);
         }
         mbar_init(fullS, 1);
-        mbar_init(emptyS, kConsumerWarps);
+        mbar_init(emptyS, NW);
+        for (int s = 0; s < kStages; ++s) fxe[s] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -221,7 +201,8 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     const int oc = p.o - p.c;
     const uint64_t ocmask = (1ull << oc) - 1ull;
     const bool has_stream = p.stream != nullptr;
-    const bool dfm = (sizeof(T) == sizeof(double)) && p.df != 0;  // FP32-pair flip sums
+    const bool fxm = (sizeof(T) == sizeof(double)) && p.fx != 0;  // fixed-point flip sums
+    const bool fx_defer = fxm && !p.first && has_stream;            // flips x field + partial in one FMA
 
     auto coords = [&](long long t, int *crd) {
         if (p.rank == 3) {
@@ -291,19 +272,22 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
     const T bsT = (p.first && has_stream) ? (T)(-eb / sv) : (T)1;
     const T svT = (T)sv;
     const int nmine =
-        tid < nvec ? ((nvec - 1 - tid) / kPassThreads + 1 < kBV ? (nvec - 1 - tid) / kPassThreads + 1 : kBV) : 0;
-    const bool full_tile = (nmine == kBV);
-    auto gidx = [&](uint64_t base, int q) -> uint64_t {  // global 16-byte vector index of tile vector q
-        const int li = q << LOGVE;
-        return (base | ((uint64_t)(li >> p.c) << p.o) | ((uint64_t)li & cmask)) >> LOGVE;
-    };
+        tid < nvec ? ((nvec - 1 - tid) / NT + 1 < BV ? (nvec - 1 - tid) / NT + 1 : BV) : 0;
+    const bool full_tile = (nmine == BV);
+    // Output vector index of tile vector ii*NT + tid.  The local-to-global bit map
+    // li -> ((li >> c) << o) | (li & cmask) sends disjoint bit sets to disjoint
+    // ones, and the ii part (a multiple of NT*VE >= 2^c, checked at launch) to
+    // ii * (NT*VE << (o - c)): one part per thread, one uniform stride.
+    const uint64_t tli = (uint64_t)tid << LOGVE;
+    const uint64_t gtid = (((tli >> p.c) << p.o) | (tli & cmask)) >> LOGVE;
+    const uint64_t gstep = (((uint64_t)NT << LOGVE) << (p.o - p.c)) >> LOGVE;
 
     // E_ll of this thread's amplitudes: they sit at the same low bits in every
     // tile of the first pass, so the table is read once per launch
-    T ell[kBV * VE];
+    T ell[BV * VE];
 #pragma unroll
-    for (int e = 0; e < kBV * VE; ++e) {
-        const int li = (((e / VE) * kPassThreads + tid) << LOGVE) + (e % VE);
+    for (int e = 0; e < BV * VE; ++e) {
+        const int li = (((e / VE) * NT + tid) << LOGVE) + (e % VE);
         ell[e] = (p.first && li < (nvec << LOGVE)) ? __ldg(&p.Ell[li]) : (T)0;
     }
     double acc_d0 = 0.0, acc_d1 = 0.0, acc_n = 0.0;
@@ -320,7 +304,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             if (!ok) {
                 if (lane == 0) atomicExch(p.err, 1);
                 failed = true;
-                if (!dfm) break;  // FP32-pair mode: every thread leaves together at the tile barrier
+                if (!fxm) break;  // fixed-point mode: every thread leaves together at the tile barrier
             }
         }
         if (warp == 0 && lane == 0 && p.pf > 0) {
@@ -357,81 +341,115 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
         const T *tcur = tab + s * kTab;
         const uint64_t tt = (uint64_t)t;
         const uint64_t base = ((tt >> oc) << (p.o + p.g)) | ((tt & ocmask) << p.c);
-        {
-            const bool okw = mbar_wait(&fullU[s], (unsigned)((n / kStages) & 1), p.err);
-            if (dfm) {
+        const uint64_t gt = (base >> LOGVE) + gtid;  // base has no bits below c >= LOGVE (or is a multiple of the tile)
+        const bool okw = mbar_wait(&fullU[s], (unsigned)((n / kStages) & 1), p.err);
+        if (!fxm && !okw) {
+            atomicExch(p.err, 1);
+            break;
+        }
+        const T *trow = tcur;
+        T pd0 = 0, pd1 = 0, pn = 0;
+        bool stream_ready = false;
+        // Loads and flips need no guard in a partial tile (L below the tile's bits):
+        // every index stays inside the stage, and the partners of an in-range vector
+        // are in range.  Stores, table indices and sums are guarded below.
+        A self[BV * VE];
+#pragma unroll
+        for (int i = 0; i < BV; ++i) unpackv(Ucur[i * NT + tid], &self[i * VE]);
+        int et = 0;
+        double fxs = 0.0;
+        if constexpr (sizeof(T) == sizeof(double)) {
+            if (fxm) {
+                // the tile's largest exponent (every thread, then every warp, then the CTA)
+                unsigned em = 0u;
+#pragma unroll
+                for (int i = 0; i < BV; ++i) {
+                    if (full_tile || i < nmine) {
+                        const unsigned a = fx_expo(self[i].x), b = fx_expo(self[i].y);
+                        em = max(em, max(a, b));
+                    }
+                }
+                em = __reduce_max_sync(0xffffffffu, em);
+                if (lane == 0) atomicMax(&fxe[s], em);
                 if (__syncthreads_or(!okw || failed)) {
                     atomicExch(p.err, 1);
                     failed = true;
                     break;
                 }
-            } else if (!okw) {
-                atomicExch(p.err, 1);
-                break;
-            }
-        }
-        const T *trow = tcur;
-        T pd0 = 0, pd1 = 0, pn = 0;
-        bool stream_ready = false;
-        A self[kBV * VE];
+                et = (int)*reinterpret_cast<volatile unsigned *>(&fxe[s]);
+                fxs = fx_scale(p.fxh, et);
+                // this thread's amplitudes onto the tile's grid, in place; the flips
+                // below read every partner in that form
+                longlong2 *Ux = reinterpret_cast<longlong2 *>(const_cast<V *>(Ucur));
 #pragma unroll
-        for (int i = 0; i < kBV; ++i) {
-            if (full_tile || i < nmine) unpackv(Ucur[i * kPassThreads + tid], &self[i * VE]);
-            else unpackv(V{}, &self[i * VE]);
-        }
-        if constexpr (sizeof(T) == sizeof(double)) {
-            if (dfm) {
-                // this thread's amplitudes to (re_hi, re_lo, im_hi, im_lo) in place; the
-                // flips below read every partner in that form
-                float4 *Uf = reinterpret_cast<float4 *>(const_cast<V *>(Ucur));
-#pragma unroll
-                for (int i = 0; i < kBV; ++i) {
+                for (int i = 0; i < BV; ++i) {
                     if (full_tile || i < nmine) {
-                        const double2 a = self[i];
-                        float4 f;
-                        split_df(a.x, f.x, f.y);
-                        split_df(a.y, f.z, f.w);
-                        Uf[i * kPassThreads + tid] = f;
+                        longlong2 f;
+                        f.x = fx_from(self[i].x, et);
+                        f.y = fx_from(self[i].y, et);
+                        Ux[i * NT + tid] = f;
                     }
                 }
                 __syncthreads();
+                if (tid == 0) fxe[s] = 0u;  // every thread has read it; stage s is refilled after the next tile's barriers
             }
         }
         // accumulate in two halves of eight vectors; all four bits of i are
         // flipped in registers
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-            constexpr int NH = kBV / 2;
+            constexpr int NH = BV / 2;
             A r[NH * VE];
 #pragma unroll
             for (int e = 0; e < NH * VE; ++e) r[e] = azero(T(0));
             if constexpr (sizeof(T) == sizeof(double)) {
-                if (dfm) {
-                    // complex128, one field on every flipped bit: sum of the flipped
-                    // partners on FP32 pairs with exact error terms, then one FP64 multiply
-                    const float4 *Uf = reinterpret_cast<const float4 *>(Ucur);
-                    DfAcc ar[NH], ai[NH];
+                if (fxm) {
+                    // complex128, one field on every flipped bit: exact integer sum of
+                    // the flipped partners, then one FP64 multiply by the field
+                    const longlong2 *Ux = reinterpret_cast<const longlong2 *>(Ucur);
+                    long long ar[NH], ai[NH];
 #pragma unroll
-                    for (int i = 0; i < NH; ++i) ar[i] = ai[i] = DfAcc{0.0f, 0.0f, 0.0f};
-                    for (int lb = p.c; lb < tbits; ++lb) {
+                    for (int i = 0; i < NH; ++i) ar[i] = ai[i] = 0ll;
+                    // thread bits: the partner of vector ii*NT + tid is ii*NT + (tid ^ 2^lb)
+                    const int tb1 = tbits < TBITS ? tbits : TBITS;
+                    for (int lb = p.c; lb < tb1; ++lb) {
+                        const longlong2 *Uf = Ux + (tid ^ (1 << lb));
 #pragma unroll
                         for (int i = 0; i < NH; ++i) {
-                            const int ii = hh * NH + i;
-                            if (full_tile || ii < nmine) {
-                                const float4 v = Uf[(ii * kPassThreads + tid) ^ (1 << lb)];
-                                df_add(ar[i], v.x, v.y);
-                                df_add(ai[i], v.z, v.w);
+                            const longlong2 v = Uf[(hh * NH + i) * NT];
+                            ar[i] += v.x;
+                            ai[i] += v.y;
+                        }
+                    }
+                    // vector-index bits: the partner of ii is ii ^ 2^j
+#pragma unroll
+                    for (int j = 0; j < IBITS; ++j) {
+                        const int lb = TBITS + j;
+                        if (lb >= p.c && lb < tbits) {
+#pragma unroll
+                            for (int i = 0; i < NH; ++i) {
+                                const longlong2 v = Ux[((hh * NH + i) ^ (1 << j)) * NT + tid];
+                                ar[i] += v.x;
+                                ai[i] += v.y;
                             }
                         }
                     }
+                    if (fx_defer) {  // later passes: the field is applied with the partial sum below
 #pragma unroll
-                    for (int i = 0; i < NH; ++i) {
-                        r[i].x = p.dfh * df_value(ar[i]);
-                        r[i].y = p.dfh * df_value(ai[i]);
+                        for (int i = 0; i < NH; ++i) {
+                            r[i].x = __ll2double_rn(ar[i]);
+                            r[i].y = __ll2double_rn(ai[i]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < NH; ++i) {
+                            r[i].x = fxs * __ll2double_rn(ar[i]);
+                            r[i].y = fxs * __ll2double_rn(ai[i]);
+                        }
                     }
                 }
             }
-            if (!dfm && VE == 2 && p.c == 0) {
+            if (!fxm && VE == 2 && p.c == 0) {
                 // bit 0 lives inside the 16-byte vector
                 const K f = mkcoef(p.hb[p.o]);
 #pragma unroll
@@ -442,9 +460,9 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
 #pragma unroll
-            for (int j = 0; j < kIBits; ++j) {
-                const int lb = LOGVE + kTBits + j;  // local bit carried by bit j of i
-                if (!dfm && lb >= p.c && lb < tbits) {
+            for (int j = 0; j < IBITS; ++j) {
+                const int lb = LOGVE + TBITS + j;  // local bit carried by bit j of i
+                if (!fxm && lb >= p.c && lb < tbits) {
                     const K f = mkcoef(p.hb[p.o + lb - p.c]);
 #pragma unroll
                     for (int i = 0; i < NH; ++i) {
@@ -455,52 +473,55 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
             // flips of the eight bits of tid: neighbour vectors from shared memory
-            if (!dfm) {
+            if (!fxm) {
                 const int lb0 = p.c > LOGVE ? p.c : LOGVE;
-                const int lb1 = tbits < LOGVE + kTBits ? tbits : LOGVE + kTBits;
+                const int lb1 = tbits < LOGVE + TBITS ? tbits : LOGVE + TBITS;
                 for (int lb = lb0; lb < lb1; ++lb) {
                     const K f = mkcoef(p.hb[p.o + lb - p.c]);
-                    const int flip = 1 << (lb - LOGVE);
+                    // the flipped bit is a thread bit: the partner of ii*NT + tid is ii*NT + (tid ^ flip)
+                    const V *Uf = Ucur + (tid ^ (1 << (lb - LOGVE)));
 #pragma unroll
-                    for (int h4 = 0; h4 < NH / kHB; ++h4) {
-                        V v[kHB];
+                    for (int h4 = 0; h4 < NH / HB; ++h4) {
+                        V v[HB];
 #pragma unroll
-                        for (int i = 0; i < kHB; ++i) {
-                            const int ii = hh * NH + h4 * kHB + i;
-                            if (full_tile || ii < nmine) v[i] = Ucur[(ii * kPassThreads + tid) ^ flip];
-                            else v[i] = V{};
+                        for (int i = 0; i < HB; ++i) {
+                            v[i] = Uf[(hh * NH + h4 * HB + i) * NT];
                         }
 #pragma unroll
-                        for (int i = 0; i < kHB; ++i) {
+                        for (int i = 0; i < HB; ++i) {
                             A x[VE];
                             unpackv(v[i], x);
 #pragma unroll
-                            for (int e = 0; e < VE; ++e) afma(f, x[e], r[(h4 * kHB + i) * VE + e]);
+                            for (int e = 0; e < VE; ++e) afma(f, x[e], r[(h4 * HB + i) * VE + e]);
                         }
                     }
                 }
             }
             if (p.first) {
-                // E(b) - a = E_ll (registers) + TA (low ta bits) + TB (bits above ta) - a
+                // E(b) - a = E_ll (registers) + TA (low ta bits) + TB (bits above ta) - a;
+                // the low ta <= 6 bits of li are those of (tid << LOGVE) + e for every ii
                 const int tmask = (1 << p.ta) - 1;
+                T tav[VE];
+#pragma unroll
+                for (int e = 0; e < VE; ++e) tav[e] = trow[((tid << LOGVE) + e) & tmask];
 #pragma unroll
                 for (int i = 0; i < NH; ++i) {
                     const int ii = hh * NH + i;
                     if (full_tile || ii < nmine) {
-                        const int li = (ii * kPassThreads + tid) << LOGVE;
+                        const int li = (ii * NT + tid) << LOGVE;
                         const T tbv = trow[64 + (li >> p.ta)] - aT;
 #pragma unroll
                         for (int e = 0; e < VE; ++e) {
-                            const T E = ell[ii * VE + e] + trow[(li + e) & tmask] + tbv;
+                            const T E = ell[ii * VE + e] + tav[e] + tbv;
                             afma(mkcoef(E), self[ii * VE + e], r[i * VE + e]);
                         }
                     }
                 }
             }
             if (hh == 1) {
-                // u stage s is no longer read by this warp (its FP32-pair stores
+                // u stage s is no longer read by this warp (its fixed-point stores
                 // are ordered before the next bulk copy into the stage)
-                if (dfm) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (fxm) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&emptyU[s]);
             }
@@ -509,7 +530,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                     if (!mbar_wait(fullS, (unsigned)(n & 1), p.err)) {
                         atomicExch(p.err, 1);
                         failed = true;
-                        if (!dfm) break;  // FP32-pair mode: leave at the next tile barrier
+                        if (!fxm) break;  // fixed-point mode: leave at the next tile barrier
                     }
                     stream_ready = true;
                 }
@@ -517,12 +538,18 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
 #pragma unroll
                 for (int i = 0; i < NH; ++i) {
                     const int ii = hh * NH + i;
-                    if (full_tile || ii < nmine) {
-                        A x[VE];
-                        unpackv(S[ii * kPassThreads + tid], x);
-#pragma unroll
-                        for (int e = 0; e < VE; ++e) afma(bsK, x[e], r[i * VE + e]);
+                    A x[VE];
+                    unpackv(S[ii * NT + tid], x);
+                    if constexpr (sizeof(T) == sizeof(double)) {
+                        if (fx_defer) {
+                            // r = field x unit x (integer flip sum) + partial
+                            r[i].x = fma(fxs, r[i].x, x[0].x);
+                            r[i].y = fma(fxs, r[i].y, x[0].y);
+                            continue;
+                        }
                     }
+#pragma unroll
+                    for (int e = 0; e < VE; ++e) afma(bsK, x[e], r[i * VE + e]);
                 }
                 if (hh == 1) {
                     __syncwarp();
@@ -539,8 +566,22 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 for (int i = 0; i < NH; ++i) {
                     const int ii = hh * NH + i;
                     if (full_tile || ii < nmine) {
-                        if (p.last) st_stream(&p.out[gidx(base, ii * kPassThreads + tid)], packv(&r[i * VE]));
-                        else p.out[gidx(base, ii * kPassThreads + tid)] = packv(&r[i * VE]);
+                        const uint64_t gi = gt + (uint64_t)ii * gstep;
+                        if (p.last) st_stream(&p.out[gi], packv(&r[i * VE]));
+                        else p.out[gi] = packv(&r[i * VE]);
+                    }
+                }
+            }
+            if (p.last && p.epilogue != EPI_PLAIN && !full_tile) {
+                // partial tile: the vectors past the end hold stale shared memory
+#pragma unroll
+                for (int i = 0; i < NH; ++i) {
+                    if (hh * NH + i >= nmine) {
+#pragma unroll
+                        for (int e = 0; e < VE; ++e) {
+                            r[i * VE + e] = azero(T(0));
+                            self[(hh * NH + i) * VE + e] = azero(T(0));
+                        }
                     }
                 }
             }
@@ -562,10 +603,28 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
                 }
             }
         }
-        if (failed && !dfm) break;
-        acc_d0 += (double)pd0;
-        acc_d1 += (double)pd1;
-        acc_n += (double)pn;
+        if (failed && !fxm) break;
+        if (p.last && p.epilogue != EPI_PLAIN) {
+            if constexpr (sizeof(T) == sizeof(float)) {
+                // the tile's FP32 sums of the warp first (fixed order), then one FP64
+                // add per warp: FP64 issues at 2 lanes per clock per SM on this part
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    pd0 += __shfl_xor_sync(0xffffffffu, pd0, off);
+                    pd1 += __shfl_xor_sync(0xffffffffu, pd1, off);
+                    pn += __shfl_xor_sync(0xffffffffu, pn, off);
+                }
+                if (lane == 0) {
+                    acc_d0 += (double)pd0;
+                    acc_d1 += (double)pd1;
+                    acc_n += (double)pn;
+                }
+            } else {
+                acc_d0 += (double)pd0;
+                acc_d1 += (double)pd1;
+                acc_n += (double)pn;
+            }
+        }
     }
 
     if (failed && warp == 0 && lane == 0) {
@@ -584,7 +643,7 @@ __global__ void __launch_bounds__(kHpsiThreads, 1)
             acc_n += __shfl_xor_sync(0xffffffffu, acc_n, off);
         }
         if (lane == 0) {
-            double *dst = p.partials + 4 * ((size_t)blockIdx.x * kConsumerWarps + warp);
+            double *dst = p.partials + 4 * ((size_t)blockIdx.x * NW + warp);
             dst[0] = acc_d0 * sv;
             dst[1] = acc_d1 * sv;
             dst[2] = acc_n;
@@ -695,36 +754,40 @@ PassPlan make_plan(int L, int prec) {
 
 static size_t pass_smem() {
     return (size_t)(kStages + 1) * (1u << kTileBytesLog2) + (size_t)kStages * kTab * sizeof(double) +
-           (2 * kStages + 2) * sizeof(unsigned long long);
+           (2 * kStages + 2) * sizeof(unsigned long long) + 16;
 }
 
-template <typename T>
+template <typename T, int BV>
 static int grid_for(Handle *h, long long ntiles) {
     static int occ = -1;
     if (occ < 0) {
-        cudaFuncSetAttribute(hpsi_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem());
+        cudaFuncSetAttribute(hpsi_pass_kernel<T, BV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem());
         // smallest shared-memory carve-out that fits (the rest stays L1 for the E_ll table)
         int maxsm = 0;
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
         if (maxsm > 0) {
             int pct = (int)((pass_smem() + 2048) * 100 / (size_t)maxsm) + 1;
             if (pct > 100) pct = 100;
-            cudaFuncSetAttribute(hpsi_pass_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            cudaFuncSetAttribute(hpsi_pass_kernel<T, BV>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
         }
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hpsi_pass_kernel<T>, kHpsiThreads, pass_smem());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hpsi_pass_kernel<T, BV>, kTileV / BV, pass_smem());
         occ = n > 0 ? n : 1;
     }
     long long g = (long long)occ * h->nsm;
     return (int)(ntiles < g ? ntiles : g);
 }
 
+static int pass_bv(const Handle *h) { return h->pass_threads == 512 ? 8 : 16; }
+
 int hpsi_grid(Handle *h, int pass) {
     const long long nt = h->plan.p[pass].ntiles;
-    return h->prec == OSMPS_FP64 ? grid_for<double>(h, nt) : grid_for<float>(h, nt);
+    const bool w = pass_bv(h) == 8;
+    if (h->prec == OSMPS_FP64) return w ? grid_for<double, 8>(h, nt) : grid_for<double, 16>(h, nt);
+    return w ? grid_for<float, 8>(h, nt) : grid_for<float, 16>(h, nt);
 }
 
-int hpsi_partials_per_cta() { return kConsumerWarps; }
+int hpsi_partials_per_cta() { return kMaxPassWarps; }
 
 // ---- tensor maps ----
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -890,26 +953,34 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.pf = h->prefetch;
         p.tile_bytes = (unsigned)((1u << (d.c + d.g)) * h->esize);
         for (int k = 0; k <= kMaxL; ++k) p.hb[k] = (T)h->hbit[k];
-        // complex128 passes that flip many bits sharing one field sum on FP32 pairs:
-        // the split and recombination cost about as much as six FP64 flips, and
-        // the FP32-pair code is issue-bound at this kernel's 8 warps per SM, so
-        // only the passes of ten or more flipped bits (the first) gain
-        p.df = 0;
-        p.dfh = 0.0;
-        if (sizeof(T) == sizeof(double) && h->flip_pairs && d.g >= 10) {
+        // complex128 passes whose flipped bits share one field sum the partners in
+        // fixed point (flip_fixed = the fewest flipped bits for which it is used; 0 = never)
+        p.fx = 0;
+        p.fxh = 0.0;
+        if (sizeof(T) == sizeof(double) && h->flip_fixed > 0 && d.g >= h->flip_fixed) {
             bool uniform = true;
             for (int k = d.o + 1; k < d.o + d.g; ++k) uniform = uniform && (h->hbit[k] == h->hbit[d.o]);
             if (uniform) {
-                p.df = 1;
-                p.dfh = h->hbit[d.o];
+                p.fx = 1;
+                p.fxh = h->hbit[d.o];
             }
         }
-        const int grid = grid_for<T>(h, d.ntiles);
-        hpsi_pass_kernel<T><<<grid, kHpsiThreads, pass_smem(), h->stream>>>(tm_u, tm_s, p);
+        // the kernel's output indexing needs the vector-index bits above the carried chunk
+        if (((kTileV / pass_bv(h)) * (int)(16 / h->esize)) < (1 << d.c)) return cudaErrorInvalidValue;
+        int grid = 0, nw = 0;
+        if (pass_bv(h) == 8) {
+            grid = grid_for<T, 8>(h, d.ntiles);
+            nw = kTileV / 8 / 32;
+            hpsi_pass_kernel<T, 8><<<grid, kTileV / 8, pass_smem(), h->stream>>>(tm_u, tm_s, p);
+        } else {
+            grid = grid_for<T, 16>(h, d.ntiles);
+            nw = kTileV / 16 / 32;
+            hpsi_pass_kernel<T, 16><<<grid, kTileV / 16, pass_smem(), h->stream>>>(tm_u, tm_s, p);
+        }
         h->launches += 1;
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
-        if (last) nparts = grid * kConsumerWarps;
+        if (last) nparts = grid * nw;
     }
     if (nparts_out) *nparts_out = nparts;
     return cudaSuccess;

@@ -840,17 +840,22 @@ constexpr int kRayMaxN = 8192;  // one CTA sorts the spectrum in shared memory
 
 // lambda_i = sum_t part_re[i][t] + part_im[i][t] (fixed order), sorted descending,
 // rescaled by |psi|^2 / sum_i lambda_i (norm partials: 4 doubles per CTA, the
-// first is |x|^2), S = -sum lambda ln lambda.  One CTA, n a power of two.
+// first is |x|^2), S = -sum lambda ln lambda.  One CTA, n a power of two.  A
+// non-finite value or norm (the library eigen-solver has returned non-finite
+// eigenvectors for nearly rank-one rho with FP32-subnormal entries) makes S NaN,
+// which sends the caller to the singular values of M.
 __global__ void __launch_bounds__(1024) rayleigh_entropy_kernel(const double *part_re, const double *part_im, int n,
                                                                  int ntx, const double *norm_parts, int nparts,
                                                                  double *lambda, double *S) {
     extern __shared__ double lam_s[];
     __shared__ double red[32];
     __shared__ double trace_s;
+    int bad = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double v = 0.0;
         for (int t = 0; t < ntx; ++t) v += part_re[(size_t)i * ntx + t] + part_im[(size_t)i * ntx + t];
         lam_s[i] = v;
+        if (!isfinite(v)) bad = 1;
     }
     if (threadIdx.x < 32) {
         double t = 0.0;
@@ -858,8 +863,9 @@ __global__ void __launch_bounds__(1024) rayleigh_entropy_kernel(const double *pa
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
         if (threadIdx.x == 0) trace_s = t;
+        if (!isfinite(t)) bad = 1;
     }
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     // bitonic sort, descending
     for (int k = 2; k <= n; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -905,7 +911,7 @@ __global__ void __launch_bounds__(1024) rayleigh_entropy_kernel(const double *pa
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        *S = t;
+        *S = bad ? __longlong_as_double(0x7FF8000000000000ll) : t;
     }
 }
 

@@ -99,3 +99,42 @@ def test_rayleigh_not_for_fp64_or_small_blocks():
     ref = x.cpu().numpy().astype(np.complex128)
     assert abs(c.schmidt_entropy(x) - O.schmidt_entropy(ref, 12)) < TOL["mixed"]
     c.close()
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-8, 1e-19, 1e-21])
+def test_rayleigh_nearly_product_states(eps):
+    """All-up plus eps times a Gaussian state (L = 16): the Gram product's entries
+    run down into FP32 subnormals.  The default route gives a finite spectrum and
+    S within the mixed tolerance of the oracle's S of the same complex64 state
+    (falling back to the singular values where the library's eigenvectors are not
+    finite)."""
+    L = 16
+    psi = si.basis_state(L, 0) + eps * si.gaussian_state(L, 16)
+    psi = psi / np.linalg.norm(psi)
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    x = to_dev(psi, "mixed")
+    ref = x.cpu().numpy().astype(np.complex128)
+    S, lam = c.schmidt_entropy(x, spectrum=True)
+    assert np.all(np.isfinite(lam)) and math.isfinite(S)
+    assert abs(S - O.schmidt_entropy(ref, L)) < TOL["mixed"]
+    c.close()
+
+
+@pytest.mark.parametrize("threads", [256, 512])
+def test_rayleigh_on_quench_states_of_both_pass_shapes(threads):
+    """The L = 16 quench (alpha = 1.5, h = 0.8, all-up, m = 20, dt = 0.01) after 10,
+    20 and 30 steps with either H.psi CTA shape; the two shapes round differently,
+    and one of the resulting states made the library return non-finite
+    eigenvectors.  S against the oracle's S of the state the GPU holds."""
+    L = 16
+    c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    c.set_pass_threads(threads)
+    x = c.new_state()
+    c.init_basis_state(x, 0)
+    for _ in range(3):
+        c.krylov_evolve(x, 0.01, 10, 20)
+        ref = x.cpu().numpy().astype(np.complex128)
+        S, lam = c.schmidt_entropy(x, spectrum=True)
+        assert np.all(np.isfinite(lam))
+        assert abs(S - O.schmidt_entropy(ref, L)) < TOL["mixed"]
+    c.close()

@@ -19,13 +19,16 @@ def chain_for(L, Jr, hk, prec):
     return c
 
 
+@pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 7, 8, 11, 12, 13, 14, 15, 16, 17, 18, 20])
-def test_apply_H_matches_csr(L, prec):
+def test_apply_H_matches_csr(L, prec, threads):
+    """Both CTA shapes of the passes (16 or 8 vectors per thread)."""
     rng = np.random.default_rng(100 + L)
     Jr = rng.normal(size=L - 1)
     hk = rng.normal(size=L)
     c = chain_for(L, Jr, hk, prec)
+    c.set_pass_threads(threads)
     psi = si.gaussian_state(L, L)
     x = to_dev(psi, prec)
     ref = O.hamiltonian_csr(L, Jr, hk) @ x.cpu().numpy().astype(np.complex128)
@@ -89,13 +92,15 @@ def test_energy_call():
     assert abs(n2 - np.vdot(psi, psi).real) < 1e-13
 
 
+@pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("L,prec", [(24, "fp64"), (24, "mixed"), (28, "mixed"), (28, "fp64"), (30, "mixed")])
-def test_apply_H_full_size_sampled_rows(L, prec):
+def test_apply_H_full_size_sampled_rows(L, prec, threads):
     """At the workload sizes: rows sampled across the whole index range, each
-    checked against the oracle's row-definition product."""
+    checked against the oracle's row-definition product (both CTA shapes)."""
     from paper_1802_10052_gb300 import Chain
     alpha, h = (1.5, 0.8) if L != 30 else (1.0, 1.2)
     c = Chain(L, J=1.0, alpha=alpha, h=h, prec=prec)
+    c.set_pass_threads(threads)
     x = seeded_device_state(L, 28, prec)
     out = c.new_state()
     c.apply_H(x, out)
@@ -129,12 +134,13 @@ def test_prefetch_and_sm_count_do_not_change_the_product(L, prec):
     c.close()
 
 
+@pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("L", [3, 8, 12, 13, 14, 18, 20])
-@pytest.mark.parametrize("mode", [0, 1])
-def test_fp64_flip_sums_match_csr(L, mode):
-    """complex128 H.psi with the flip sums on FP32 pairs with exact error terms (mode 1, used
-    in passes of ten or more flipped bits that share one field) and on FP64 multiply-adds
-    (mode 0), uniform and site-dependent fields, against the CSR product."""
+@pytest.mark.parametrize("mode", [0, 1, 7])
+def test_fp64_flip_sums_match_csr(L, mode, threads):
+    """complex128 H.psi with the flip sums in 64-bit fixed point (mode 1: every pass whose
+    flipped bits share one field; mode 7: only passes of seven or more flipped bits) and on
+    FP64 multiply-adds (mode 0), uniform and site-dependent fields, against the CSR product."""
     from paper_1802_10052_gb300 import Chain
     rng = np.random.default_rng(500 + L)
     Jr = rng.normal(size=L - 1)
@@ -143,6 +149,7 @@ def test_fp64_flip_sums_match_csr(L, mode):
     for hk in ([0.83] * L, list(rng.normal(size=L))):
         c = chain_for(L, Jr, hk, "fp64")
         c.set_flip_sums(mode)
+        c.set_pass_threads(threads)
         out = c.new_state()
         c.apply_H(x, out)
         ref = O.hamiltonian_csr(L, Jr, hk) @ psi
@@ -152,9 +159,14 @@ def test_fp64_flip_sums_match_csr(L, mode):
         c.close()
 
 
-def test_fp64_flip_sums_wide_dynamic_range():
-    """Amplitudes spread over sixty decades (1e-30 .. 1): every output element,
-    small ones included, to 1e-12 of its own size plus 1e-30 of the largest."""
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp64_flip_sums_wide_dynamic_range(mode):
+    """Amplitudes spread over sixty decades (1e-30 .. 1).  FP64 multiply-adds (mode 0):
+    every output element, small ones included, to 1e-12 of its own size plus 1e-30 of the
+    largest.  Fixed-point sums (mode 1): each flip sum is exact up to one unit of 2^-57 of
+    its tile's largest amplitude per flipped partner (at most 12 of them), so an element may
+    also be off by 12 * 2^-57 h max|psi| plus the rounding of the sum; the whole product
+    stays within the FP64 tolerance."""
     L = 14
     rng = np.random.default_rng(77)
     psi = si.gaussian_state(L, 77) * 10.0 ** rng.uniform(-30, 0, size=1 << L)
@@ -162,10 +174,14 @@ def test_fp64_flip_sums_wide_dynamic_range():
     ref = O.RuleSetH(L, Jr, 0.8)(psi)
     from paper_1802_10052_gb300 import Chain
     c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec="fp64")
+    c.set_flip_sums(mode)
     x = to_dev(psi, "fp64")
     out = c.new_state()
     c.apply_H(x, out)
     got = to_host(out)
     bound = np.abs(O.RuleSetH(L, np.abs(Jr), 0.8)(np.abs(psi))) + np.abs(O.diagonal_energy(L, Jr, np.arange(1 << L)) * psi)
-    assert np.all(np.abs(got - ref) <= 1e-12 * bound + 1e-30 * np.max(np.abs(psi)))
+    mx = np.max(np.abs(psi))
+    fixed = 0.0 if mode == 0 else 0.8 * 12 * 2.0 ** -57 * mx
+    assert np.all(np.abs(got - ref) <= 1e-12 * bound + fixed + 1e-30 * mx)
+    assert rel(got, ref) < 1e-13
     c.close()
