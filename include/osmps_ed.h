@@ -155,6 +155,15 @@ osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);
  * 0 <= tiles <= 4.  Not from the paper (memory scheduling). */
 osmps_status osmps_ed_set_prefetch(osmps_ed_t *ed, int tiles);
 
+/* Launches of a Krylov Lanczos step without the Gram-Schmidt pass (not from
+ * the paper; scheduling).  1 (default): alpha_j is summed inside the update
+ * kernel and beta_{j+1} inside the next product's first pass (three launches
+ * per step); 0: separate single-warp control kernels (five).  The scalars are
+ * the same fixed-order sums either way, so results are bit-identical.  The
+ * ground-state search always uses the separate kernels (it reads T after every
+ * step). */
+osmps_status osmps_ed_set_lanczos_fold(osmps_ed_t *ed, int on);
+
 /* CTA shape of the H.psi passes (not from the paper; scheduling): 256 threads
  * holding 16 vectors of a 64 KiB tile each, or 512 threads holding 8 (twice the
  * warps per SM to hide latency, one more bit flipped through shared memory).

@@ -275,6 +275,10 @@ class Chain:
         flipping at least k bits (default 1), 0 = FP64 multiply-adds."""
         check(lib.osmps_ed_set_flip_sums(self._h, int(mode)), "osmps_ed_set_flip_sums")
 
+    def set_lanczos_fold(self, on):
+        """Krylov Lanczos steps in three launches (1, default) or five (0); bit-identical."""
+        check(lib.osmps_ed_set_lanczos_fold(self._h, int(on)), "osmps_ed_set_lanczos_fold")
+
     def set_pass_threads(self, threads):
         """CTA shape of the H.psi passes: 256 (16 vectors per thread) or 512 (8)."""
         check(lib.osmps_ed_set_pass_threads(self._h, int(threads)), "osmps_ed_set_pass_threads")

@@ -56,6 +56,7 @@ SIGNATURES = {
     "osmps_ed_set_prefetch": (_I, [_P, _I]),
     "osmps_ed_set_flip_sums": (_I, [_P, _I]),
     "osmps_ed_set_pass_threads": (_I, [_P, _I]),
+    "osmps_ed_set_lanczos_fold": (_I, [_P, _I]),
     "osmps_ed_set_entropy_method": (_I, [_P, _I]),
     "osmps_ed_launch_count": (_I, [_P, C.POINTER(C.c_int64)]),
     "osmps_ed_probe_wait": (_I, [_P, _D, _I]),

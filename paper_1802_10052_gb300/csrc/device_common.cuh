@@ -67,6 +67,16 @@ __device__ __forceinline__ float2 tocx(unsigned long long a) {
 }
 __device__ __forceinline__ double2 tocx(const double2 &a) { return a; }
 
+// fixed-order sum of partials[i*stride + k], i < n, done by one warp (every lane
+// returns the sum; the same order in every CTA and kernel that calls it)
+static __device__ __forceinline__ double warp_sum_partials(const double *partials, int n, int stride, int k) {
+    double s = 0.0;
+    for (int i = threadIdx.x & 31; i < n; i += 32) s += partials[(size_t)i * stride + k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+}
+
 // ---- mbarrier / TMA primitives (PTX) ----
 __device__ __forceinline__ unsigned smem_u32(const void *ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {

@@ -252,8 +252,13 @@ __global__ void ctl_finish_energy_kernel(KrylovCtl *ctl, const double *partials,
 
 // One Lanczos iteration j: w = H v_j - beta_j v_{j-1} (fused), alpha_j,
 // u_{j+1} = w - alpha_j v_j, optional Gram-Schmidt against v_0..v_j, beta_{j+1}.
-osmps_status lanczos_iteration(Handle *h, int j, int reorth) {
+// Folded (allow_fold, no Gram-Schmidt pass, handle setting on): alpha_j is
+// summed inside the update and beta_{j+1} inside the next product's first pass,
+// so a step is three launches; lanczos_finish stores the last beta.  Every
+// scalar is the same fixed-order sum as in the unfolded sequence.
+osmps_status lanczos_iteration(Handle *h, int j, int reorth, bool allow_fold) {
     int np = 0;
+    const bool fold = allow_fold && !reorth && h->fold_ctl;
     HpsiArgs a{};
     a.u = h->V[j];
     a.uprev = j > 0 ? h->V[j - 1] : nullptr;
@@ -264,7 +269,17 @@ osmps_status lanczos_iteration(Handle *h, int j, int reorth) {
     a.m_eff = &h->ctl->m_eff;
     a.stop_index = j;
     a.epilogue = EPI_KRYLOV;
+    if (fold && j > 0) {
+        a.fold_ctl = h->ctl;
+        a.fold_parts = h->partials_upd;
+        a.fold_nparts = vec_grid(h);
+    }
     CK(launch_hpsi_timed(h, a, &np));
+    if (fold) {
+        int nu = 0;
+        CK(launch_update_folded(h, h->V[j + 1], h->V[j], h->ctl, j, h->partials, np, h->partials_upd, &nu));
+        return OSMPS_OK;
+    }
     CK(launch_ctl_after_hpsi(h, h->ctl, h->partials, np, j));
     CK(launch_update(h, h->V[j + 1], h->V[j], h->ctl, j, h->partials, &np));
     if (reorth) {
@@ -273,6 +288,14 @@ osmps_status lanczos_iteration(Handle *h, int j, int reorth) {
         CK(launch_reorth_update(h, h->V_dev, j + 1, h->V[j + 1], h->ctl, j, h->partials2, nd, h->partials, &np));
     }
     CK(launch_ctl_after_update(h, h->ctl, h->partials, np, j, 0));
+    return OSMPS_OK;
+}
+
+// After m folded iterations: beta_m, its breakdown test and scale_m (the step
+// that a next product's first pass would otherwise have done).
+osmps_status lanczos_finish(Handle *h, int m, int reorth) {
+    if (reorth || !h->fold_ctl) return OSMPS_OK;
+    CK(launch_ctl_after_update(h, h->ctl, h->partials_upd, vec_grid(h), m - 1, 0));
     return OSMPS_OK;
 }
 
@@ -287,7 +310,8 @@ osmps_status krylov_basis(Handle *h, void *v0, int m) {
     int np = 0;
     CK(launch_norm2(h, v0, h->partials, &np));
     CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, m));
-    for (int j = 0; j < m; ++j) CKS(lanczos_iteration(h, j, h->reorth));
+    for (int j = 0; j < m; ++j) CKS(lanczos_iteration(h, j, h->reorth, true));
+    CKS(lanczos_finish(h, m, h->reorth));
     return OSMPS_OK;
 }
 
@@ -356,6 +380,7 @@ void destroy_handle(Handle *h) {
     dev_free(h, h->Fhh, 0);
     dev_free(h, h->Tab, 0);
     dev_free(h, h->partials, 0);
+    dev_free(h, h->partials_upd, 0);
     dev_free(h, h->partials2, 0);
     dev_free(h, h->dscratch, 0);
     dev_free(h, h->ctl, 0);
@@ -683,6 +708,7 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
     hd->entropy_method = ENT_AUTO;
     hd->flip_fixed = 1;
     hd->pass_threads = 512;
+    hd->fold_ctl = 1;
     hd->prefetch = (prec == OSMPS_FP64) ? 0 : 1;  // FP64 passes are bound by the FP64 pipe, not by latency
     cudaError_t err = cudaGetDevice(&hd->device);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&hd->nsm, cudaDevAttrMultiProcessorCount, hd->device);
@@ -703,6 +729,8 @@ osmps_status osmps_ed_create(int L, const double *couplings, double J, double al
         const size_t gh = (size_t)hd->nsm * 2 * hpsi_partials_per_cta();
         hd->partials_cap = (gh > g ? gh : g) * 4;
         hd->partials = (double *)dev_alloc(hd, sizeof(double) * hd->partials_cap, &err);
+        if (err != cudaSuccess) break;
+        hd->partials_upd = (double *)dev_alloc(hd, sizeof(double) * g * 4, &err);
         if (err != cudaSuccess) break;
         const size_t zneed = (g + 1) * ((size_t)(L * L + L + 1) + 4096);
         const size_t dneed = g * 2 * (kMaxLanczos + 1);
@@ -789,6 +817,12 @@ osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method) {
 osmps_status osmps_ed_set_flip_sums(osmps_ed_t *ed, int mode) {
     if (ed == nullptr || mode < 0 || mode > kMaxL) return OSMPS_EINVAL;
     ed->h.flip_fixed = mode;
+    return OSMPS_OK;
+}
+
+osmps_status osmps_ed_set_lanczos_fold(osmps_ed_t *ed, int on) {
+    if (ed == nullptr || (on != 0 && on != 1)) return OSMPS_EINVAL;
+    ed->h.fold_ctl = on;
     return OSMPS_OK;
 }
 
@@ -902,7 +936,8 @@ osmps_status osmps_ed_krylov_evolve(osmps_ed_t *ed, void *psi, double dt, int ns
     CK(launch_norm2(h, psi, h->partials, &np));
     CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, m));
     for (int s = 0; s < nsteps; ++s) {
-        for (int j = 0; j < m; ++j) CKS(lanczos_iteration(h, j, h->reorth));
+        for (int j = 0; j < m; ++j) CKS(lanczos_iteration(h, j, h->reorth, true));
+        CKS(lanczos_finish(h, m, h->reorth));
         CK(launch_tridiag_exp(h, h->ctl, m, dt));
         CK(launch_combine(h, h->V_dev, m, psi, h->ctl, h->partials, &np));
         CK(launch_ctl_after_norm(h, h->ctl, h->partials, np, m));
@@ -934,7 +969,7 @@ osmps_status osmps_ed_lanczos_ground(osmps_ed_t *ed, void *psi, double tol, int 
     int done_iters = 0;
     osmps_status result = OSMPS_ENOCONV;
     for (int j = 0; j < max_iter - 1; ++j) {
-        CKS(lanczos_iteration(h, j, reorth));
+        CKS(lanczos_iteration(h, j, reorth, false));  // T is read after every step
         done_iters = j + 1;
         CK(launch_tridiag_ground(h, h->ctl, j + 1));
         CKS(read_scalars(h, CTL_OFF(theta), CTL_OFF(m_eff) + sizeof(int) - CTL_OFF(theta)));

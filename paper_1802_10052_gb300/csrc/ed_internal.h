@@ -74,6 +74,12 @@ struct HpsiArgs {
     const int *m_eff;          // skip the launch when *m_eff <= stop_index
     int stop_index;
     int epilogue;
+    // Lanczos step stop_index >= 1 without a control kernel before it: the first
+    // pass forms beta, scale and the epilogue scalars of this step from the
+    // update's partial |u|^2 (fixed order, every CTA alike; CTA 0 writes them)
+    KrylovCtl *fold_ctl;
+    const double *fold_parts;
+    int fold_nparts;
 };
 
 struct Handle;
@@ -93,6 +99,10 @@ cudaError_t launch_norm2(Handle *h, const void *x, double *partials, int *nparts
 cudaError_t launch_cdot(Handle *h, const void *a, const void *b, double *out_dev);
 cudaError_t launch_ctl_after_norm(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j);
 cudaError_t launch_ctl_after_hpsi(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j);
+// alpha_j from the product's partials inside the update (no control kernel):
+// hp/hnp = the H.psi epilogue partials; alpha_j written by CTA 0
+cudaError_t launch_update_folded(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, const double *hp,
+                                 int hnp, double *partials, int *nparts);
 cudaError_t launch_update(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, double *partials,
                           int *nparts);
 cudaError_t launch_ctl_after_update(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j,
@@ -185,6 +195,8 @@ struct Handle {
 
     // scratch
     double *partials;           // per-CTA partial sums
+    double *partials_upd;       // the folded Lanczos update's partial |u|^2 (read by the next product)
+    int fold_ctl;               // fold the Lanczos control kernels into the update and the next product
     size_t partials_cap;        // doubles
     double *partials2;
     size_t partials2_cap;

@@ -59,6 +59,9 @@ struct PassParams {
     int L, c, o, g, ta, first, last, epilogue, rank;
     int pf;                             // L2 prefetch distance in tiles beyond the shared-memory stages
     unsigned tile_bytes;
+    KrylovCtl *fold_ctl;                // first pass of Lanczos step stop_index >= 1: beta, scale and the
+    const double *fold_parts;           //   epilogue scalars from the update's partial |u|^2 (else null)
+    int fold_nparts;
     int fx;                             // complex128 with one field on every flipped bit: flip sums in fixed point
     double fxh;                         // that field
     T hb[kMaxL + 1];
@@ -183,6 +186,39 @@ __global__ void __launch_bounds__(kTileV / BV, 1)
     if (p.m_eff != nullptr && *p.m_eff <= p.stop_index) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Lanczos control of this step folded in (as a control kernel would do it
+    // between the update and this product): beta_j = |u_j| from the update's
+    // partials in a fixed order, breakdown test, scale and epilogue scalars;
+    // every CTA computes the same values, CTA 0 stores them for the later passes
+    __shared__ double fold_s[3];
+    __shared__ int fold_stop;
+    const bool fold = p.fold_parts != nullptr;
+    if (fold && warp == 0) {
+        const int jj = p.stop_index;
+        KrylovCtl *ctl = p.fold_ctl;
+        const double n2 = warp_sum_partials(p.fold_parts, p.fold_nparts, 4, 0);
+        if (lane == 0) {
+            const double b = sqrt(n2);
+            const double ref = fabs(ctl->alpha[jj - 1]) + ctl->beta[jj - 1];
+            const bool brk = !(b > ctl->bd_tol * ref) || !(b > 0.0);
+            fold_stop = brk ? 1 : 0;
+            fold_s[0] = brk ? 0.0 : 1.0 / b;
+            fold_s[1] = 0.0;
+            fold_s[2] = brk ? 0.0 : b * ctl->scale[jj - 1];
+            if (blockIdx.x == 0) {
+                ctl->beta[jj] = b;
+                if (brk) {
+                    ctl->m_eff = jj;  // invariant subspace: the basis ends with v_{jj-1}
+                    ctl->scale[jj] = 0.0;
+                } else {
+                    ctl->scale[jj] = 1.0 / b;
+                    ctl->epi[0] = 1.0 / b;
+                    ctl->epi[1] = 0.0;
+                    ctl->epi[2] = b * ctl->scale[jj - 1];
+                }
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&fullU[s], 1);
@@ -194,6 +230,7 @@ __global__ void __launch_bounds__(kTileV / BV, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    if (fold && fold_stop) return;  // breakdown: this step is not taken
 
     const int tbits = p.c + p.g;
     const int nvec = (1 << tbits) >> LOGVE;
@@ -262,7 +299,11 @@ __global__ void __launch_bounds__(kTileV / BV, 1)
     // ------------------------------ consumers ------------------------------
     const int tid = threadIdx.x;
     double sv = 1.0, ea = 0.0, eb = 0.0;
-    if (p.epi != nullptr) {
+    if (fold) {
+        sv = fold_s[0];
+        ea = fold_s[1];
+        eb = fold_s[2];
+    } else if (p.epi != nullptr) {
         sv = p.epi[0];
         ea = p.epi[1];
         eb = p.epi[2];
@@ -937,6 +978,11 @@ static cudaError_t launch_hpsi_t(Handle *h, const HpsiArgs &a, int *nparts_out) 
         p.Tab = reinterpret_cast<const T *>(h->Tab);
         p.epi = a.epi;
         p.partials = a.partials;
+        if (i == 0 && a.fold_parts != nullptr) {
+            p.fold_ctl = a.fold_ctl;
+            p.fold_parts = a.fold_parts;
+            p.fold_nparts = a.fold_nparts;
+        }
         p.m_eff = a.m_eff;
         p.err = &h->ctl->error;
         p.stop_index = a.stop_index;

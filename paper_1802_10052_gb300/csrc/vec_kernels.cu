@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "ed_internal.h"
+#include "device_common.cuh"
 
 namespace osmps {
 
@@ -64,14 +65,6 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double *dst) {
     __syncthreads();
 }
 
-// fixed-order sum of partials[i*stride + k], i < n, done by one warp
-__device__ double warp_sum_partials(const double *partials, int n, int stride, int k) {
-    double s = 0.0;
-    for (int i = threadIdx.x & 31; i < n; i += 32) s += partials[(size_t)i * stride + k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    return s;
-}
 
 // ---------------------------------------------------------------------------
 // elementary streaming kernels
@@ -149,15 +142,30 @@ __global__ void cdot_finish_kernel(const double *partials, int nparts, double *o
     }
 }
 
-// u_{j+1} = w - alpha_j scale_j u_j (in place on w) and partial |u_{j+1}|^2
+// u_{j+1} = w - alpha_j scale_j u_j (in place on w) and partial |u_{j+1}|^2.
+// With hp != null, alpha_j is first summed here from the product's partials
+// (the same fixed order as the control kernel it replaces, in every CTA; CTA 0
+// stores it).
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) update_kernel(typename VecT<T>::v *w, const typename VecT<T>::v *u,
-                                                             uint64_t nvec, const KrylovCtl *ctl, int j,
-                                                             double *partials) {
+                                                             uint64_t nvec, KrylovCtl *ctl, int j,
+                                                             const double *hp, int hnp, double *partials) {
     typedef typename VecT<T>::v V;
     constexpr int VE = VecT<T>::VE;
     if (ctl->m_eff <= j) return;
-    const T a = (T)(ctl->alpha[j] * ctl->scale[j]);
+    __shared__ double alpha_s;
+    if (hp != nullptr) {
+        if (threadIdx.x < 32) {
+            const double d = warp_sum_partials(hp, hnp, 4, 0);
+            if (threadIdx.x == 0) {
+                alpha_s = d;
+                if (blockIdx.x == 0) ctl->alpha[j] = d;
+            }
+        }
+        __syncthreads();
+    }
+    const double alpha = hp != nullptr ? alpha_s : ctl->alpha[j];
+    const T a = (T)(alpha * ctl->scale[j]);
     double acc[1] = {0.0};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t q0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q0 < nvec; q0 += 4 * stride) {
@@ -694,18 +702,28 @@ cudaError_t launch_ctl_after_hpsi(Handle *h, KrylovCtl *ctl, const double *parti
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, double *partials,
-                          int *nparts) {
+static cudaError_t launch_update_any(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, const double *hp,
+                                     int hnp, double *partials, int *nparts) {
     const int g = vec_grid(h);
     if (h->prec == OSMPS_FP64)
         update_kernel<double><<<g, kVecThreads, 0, h->stream>>>((double2 *)w, (const double2 *)u, nvec_of(h), ctl,
-                                                                 j, partials);
+                                                                 j, hp, hnp, partials);
     else
         update_kernel<float><<<g, kVecThreads, 0, h->stream>>>((float4 *)w, (const float4 *)u, nvec_of(h), ctl, j,
-                                                                partials);
+                                                                hp, hnp, partials);
     *nparts = g;
     h->launches += 1;
     return cudaGetLastError();
+}
+
+cudaError_t launch_update(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, double *partials,
+                          int *nparts) {
+    return launch_update_any(h, w, u, ctl, j, nullptr, 0, partials, nparts);
+}
+
+cudaError_t launch_update_folded(Handle *h, void *w, const void *u, KrylovCtl *ctl, int j, const double *hp,
+                                 int hnp, double *partials, int *nparts) {
+    return launch_update_any(h, w, u, ctl, j, hp, hnp, partials, nparts);
 }
 
 cudaError_t launch_ctl_after_update(Handle *h, KrylovCtl *ctl, const double *partials, int nparts, int j, int) {

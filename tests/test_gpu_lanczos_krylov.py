@@ -192,3 +192,69 @@ def test_lrqi_quench_L24_two_steps_vs_oracle():
             assert abs(sz[k - 1] - want) < TOL[prec]
         del c, x
         torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# Lanczos steps in three launches (control scalars summed inside the update and
+# the next product) against the five-launch sequence
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("L", [10, 16, 24])
+def test_lanczos_fold_is_bit_identical(L, prec):
+    """Krylov evolution (alpha = 1.5, h = 0.8, all-up, m = 20, dt = 0.01, 5 steps) with the
+    control kernels folded and not: the same fixed-order sums, so the same bits, also
+    for the error estimate."""
+    out = []
+    for fold in (1, 0):
+        c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+        c.set_lanczos_fold(fold)
+        x = c.new_state()
+        c.init_basis_state(x, 0)
+        err = c.krylov_evolve(x, 0.01, 5, 20)
+        out.append((x.clone(), err))
+        c.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lanczos_fold_breakdown_on_an_eigenstate(prec):
+    """h = 0: a basis state is an eigenstate, the Krylov space breaks down after one
+    vector (the folded test runs in the second product's first pass).  exp(-iE dt)|b>
+    for E the diagonal energy, folded and not, bit-identical."""
+    L = 14
+    b = 0b10110011100101
+    res = []
+    for fold in (1, 0):
+        c = Chain(L, J=1.0, alpha=1.5, h=0.0, prec=prec)
+        c.set_lanczos_fold(fold)
+        x = c.new_state()
+        c.init_basis_state(x, b)
+        c.krylov_evolve(x, 0.05, 3, 20)
+        res.append(x.clone())
+        c.close()
+    assert torch.equal(res[0], res[1])
+    E = O.diagonal_energy(L, O.coupling_table(L, 1.0, 1.5), np.array([b]))[0]
+    got = to_host(res[0])
+    ref = np.zeros(1 << L, dtype=np.complex128)
+    ref[b] = np.exp(-1j * E * 0.15)
+    assert rel(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lanczos_fold_adjoint_bit_identical(prec):
+    """The adjoint gradient builds its Krylov bases with the same steps: loss and
+    gradient bit-identical with and without the fold (L = 10, 40 steps)."""
+    L = 10
+    hs = 0.8 + 0.2 * np.sin(np.arange(40) * 0.3)
+    res = []
+    for fold in (1, 0):
+        c = Chain(L, J=1.0, alpha=1.5, h=0.8, prec=prec)
+        c.set_lanczos_fold(fold)
+        x = c.new_state()
+        c.init_basis_state(x, 0)
+        res.append(c.adjoint_grad(x, hs, 0.02, m=12))
+        c.close()
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1]) and res[0][2] == res[1][2]
