@@ -143,10 +143,23 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm);
  *      give a non-finite value (seen for nearly product states whose rho has
  *      FP32-subnormal entries).  EUNSUPPORTED where it does not apply.
  *   3  automatic (the default): complex128 takes 0 (FP64 Gram and eigenvalues
- *      meet 1e-10); complex64 takes 2 where it applies, else 1 for blocks up
- *      to 8192 rows, else 0.
+ *      meet 1e-10); complex64 takes 4 where it applies, else 2 where that
+ *      applies, else 1 for blocks up to 8192 rows, else 0.
+ *   4  dominant subspace (complex64 only; 512 <= 2^min(cut, L-cut) <= 8192):
+ *      Y = M G for a seeded random K x p block G, Q = orth(Y) (Householder),
+ *      B = Q^dag M, W the eigenvectors of B B^dag (p x p), and the Schmidt
+ *      values as Rayleigh quotients |w_i^dag B|^2 (library complex FP32 GEMMs,
+ *      QR and eigen-solver, sums in FP64).  The weight outside the subspace,
+ *      |M - Q B|_F^2, is measured directly and must stay at or below 1e-9 of
+ *      the trace (its share of S is then < 1e-7); otherwise p doubles, and past
+ *      n/2 (or on a non-finite value) the call takes method 2, then 1.  p starts
+ *      at twice the number of values above 1e-12 at the handle's previous call
+ *      (128 the first time).  The spectrum has p values and zeros after them.
+ *      Scratch (Y, B, W, Z: 2 n p + 2 p K + p^2 complex, a copy of M, solver
+ *      work) is kept by the handle.  The cost follows p: weakly entangled
+ *      states (p ~ 100) need a small fraction of the full eigen-solve.
  * osmps_ed_schmidt_entropy_async takes method 0 (also when 3 is set) and
- * returns EUNSUPPORTED for 1 and 2. */
+ * returns EUNSUPPORTED for 1, 2 and 4. */
 osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);
 
 /* L2 prefetch distance of the H.psi passes: each CTA asks L2 (TMA prefetch)

@@ -267,7 +267,8 @@ class Chain:
 
     def set_entropy_method(self, method):
         """0: eigenvalues of the Gram product; 1: singular values of M; 2: Rayleigh
-        quotients of the Gram product's eigenvectors (complex64); 3: automatic (default)."""
+        quotients of the Gram product's eigenvectors (complex64); 3: automatic (default);
+        4: Rayleigh quotients on the dominant subspace (complex64, full route as fallback)."""
         check(lib.osmps_ed_set_entropy_method(self._h, int(method)), "osmps_ed_set_entropy_method")
 
     def set_flip_sums(self, mode):

@@ -395,6 +395,7 @@ void destroy_handle(Handle *h) {
     dev_free(h, h->gram, 0);
     dev_free(h, h->gram_aux, 0);
     dev_free(h, h->solver_ws, 0);
+    dev_free(h, h->sub_ws, h->sub_ws_bytes);
     dev_free(h, h->lam_dev, 0);
 }
 
@@ -809,7 +810,7 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm) {
 }
 
 osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method) {
-    if (ed == nullptr || method < ENT_GRAM || method > ENT_AUTO) return OSMPS_EINVAL;
+    if (ed == nullptr || method < ENT_GRAM || method > ENT_SUBSPACE) return OSMPS_EINVAL;
     ed->h.entropy_method = method;
     return OSMPS_OK;
 }
@@ -1061,8 +1062,33 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
     if (method == ENT_AUTO) {
         if (h->prec == OSMPS_FP64)
             method = ENT_GRAM;
+        else if (subspace_applicable(h, cut))
+            method = ENT_SUBSPACE;
         else
             method = rayleigh_applicable(h, cut) ? ENT_RAYLEIGH : (n <= 8192 ? ENT_SVD : ENT_GRAM);
+    }
+    if (method == ENT_SUBSPACE && !subspace_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
+    if (method == ENT_SUBSPACE) {
+        if ((size_t)n + 1 > h->lam_cap) {
+            dev_free(h, h->lam_dev, h->lam_cap * sizeof(double));
+            h->lam_dev = nullptr;
+            h->lam_cap = 0;
+            cudaError_t err;
+            h->lam_dev = (double *)dev_alloc(h, sizeof(double) * (n + 1), &err);
+            if (err != cudaSuccess) return from_cuda(err);
+            h->lam_cap = n + 1;
+        }
+        const osmps_status rs = schmidt_subspace(h, psi, cut, h->lam_dev, h->lam_dev + n);
+        if (rs == OSMPS_OK) {  // S was read back (and is finite) inside
+            double Sv = 0.0;
+            CK(cudaMemcpyAsync(&Sv, h->lam_dev + n, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            if (lambda) CK(cudaMemcpyAsync(lambda, h->lam_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            if (S) *S = Sv;
+            return OSMPS_OK;
+        }
+        if (rs != OSMPS_ENOCONV && rs != OSMPS_EUNSUPPORTED) return rs;
+        method = rayleigh_applicable(h, cut) ? ENT_RAYLEIGH : ENT_SVD;  // the full route
     }
     if (method == ENT_RAYLEIGH && !rayleigh_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
     if (method == ENT_RAYLEIGH) {

@@ -10,9 +10,12 @@
 // so every amplitude costs O(1) FP64 work while the L^2 outputs are updated
 // once per tile.  All sums are FP64 in a fixed order.
 #include <cuda_runtime.h>
+#include <cublas_v2.h>  // types and prototypes only: the library is loaded at first use
 #include <cusolverDn.h>
 #include <dlfcn.h>
 #include <math.h>
+
+#include <cmath>
 
 #include <mutex>
 #include <vector>
@@ -486,6 +489,11 @@ struct SolverLib {
     decltype(&cusolverDnXsyevd) x_eig = nullptr;
     decltype(&cusolverDnXgesvd_bufferSize) x_svd_bufsize = nullptr;
     decltype(&cusolverDnXgesvd) x_svd = nullptr;
+    // Householder QR and its explicit Q (the dominant-subspace route)
+    decltype(&cusolverDnCgeqrf_bufferSize) c_geqrf_bufsize = nullptr;
+    decltype(&cusolverDnCgeqrf) c_geqrf = nullptr;
+    decltype(&cusolverDnCungqr_bufferSize) c_ungqr_bufsize = nullptr;
+    decltype(&cusolverDnCungqr) c_ungqr = nullptr;
     cusolverDnParams_t params = nullptr;  // default options, read-only after creation
 };
 static SolverLib g_solver;
@@ -518,7 +526,44 @@ static bool load_solver() {
     if (!g_solver.create_params || !g_solver.x_bufsize || !g_solver.x_eig ||
         g_solver.create_params(&g_solver.params) != CUSOLVER_STATUS_SUCCESS)
         g_solver.params = nullptr;
+    g_solver.c_geqrf_bufsize = (decltype(g_solver.c_geqrf_bufsize))dlsym(g_solver.so, "cusolverDnCgeqrf_bufferSize");
+    g_solver.c_geqrf = (decltype(g_solver.c_geqrf))dlsym(g_solver.so, "cusolverDnCgeqrf");
+    g_solver.c_ungqr_bufsize = (decltype(g_solver.c_ungqr_bufsize))dlsym(g_solver.so, "cusolverDnCungqr_bufferSize");
+    g_solver.c_ungqr = (decltype(g_solver.c_ungqr))dlsym(g_solver.so, "cusolverDnCungqr");
     g_solver.ok = true;
+    return true;
+}
+
+// cuBLAS, loaded at first use like the solver: complex FP32 GEMM (default math
+// mode: FP32 arithmetic, no TF32) and the FP64 Hermitian rank-k update
+struct BlasLib {
+    bool tried = false;
+    bool ok = false;
+    void *so = nullptr;
+    cublasHandle_t handle = nullptr;
+    decltype(&cublasCreate_v2) create = nullptr;
+    decltype(&cublasSetStream_v2) set_stream = nullptr;
+    decltype(&cublasCgemm_v2) cgemm = nullptr;
+    decltype(&cublasZherk_v2) zherk = nullptr;
+};
+static BlasLib g_blas;
+
+static bool load_blas() {
+    if (g_blas.tried) return g_blas.ok;
+    g_blas.tried = true;
+    const char *names[] = {"libcublas.so.13", "libcublas.so", "libcublas.so.12"};
+    for (const char *nm : names) {
+        g_blas.so = dlopen(nm, RTLD_NOW | RTLD_LOCAL);
+        if (g_blas.so) break;
+    }
+    if (!g_blas.so) return false;
+    g_blas.create = (decltype(g_blas.create))dlsym(g_blas.so, "cublasCreate_v2");
+    g_blas.set_stream = (decltype(g_blas.set_stream))dlsym(g_blas.so, "cublasSetStream_v2");
+    g_blas.cgemm = (decltype(g_blas.cgemm))dlsym(g_blas.so, "cublasCgemm_v2");
+    g_blas.zherk = (decltype(g_blas.zherk))dlsym(g_blas.so, "cublasZherk_v2");
+    if (!g_blas.create || !g_blas.set_stream || !g_blas.cgemm || !g_blas.zherk) return false;
+    if (g_blas.create(&g_blas.handle) != CUBLAS_STATUS_SUCCESS) return false;
+    g_blas.ok = true;
     return true;
 }
 
@@ -1006,6 +1051,296 @@ osmps_status schmidt_rayleigh(Handle *h, const void *psi, int cut, void *rho, do
                                                                                  np, lambda_dev, S_dev);
     h->launches += 1;
     return cudaGetLastError() == cudaSuccess ? OSMPS_OK : OSMPS_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Schmidt values from the dominant subspace (complex64; Sec. IV bond entropy).
+// A weakly entangled state has few Schmidt values above 1e-10 (~100 of 4096 on
+// the L = 24 quench to t = 2.5); the rest carry < 1e-8 of weight.  With M the
+// n x K block matrix of psi and G a K x p random block: Y = M G, Q = orth(Y)
+// (Householder), B = Q^dag M (FP32 GEMMs); the Schmidt values are the squared
+// singular values of B, taken as the eigenvalues of C = B B^dag formed and
+// diagonalised in FP64 (the FP32 products are exact there, so no value is lost
+// to squaring: each keeps the error 2 sigma |dB| of the singular-value route).
+// The weight left outside the subspace, |M - Q B|_F^2, is measured directly
+// (not by subtraction from the trace) and must stay at or below 1e-9 of the
+// trace; otherwise p doubles, and beyond n/2 the caller takes the full route.
+// ---------------------------------------------------------------------------
+constexpr int kSubResBlocks = 608;  // CTAs of the residual-norm partial sums
+constexpr int kSubMaxP = 768;       // largest subspace tried
+constexpr int kSubSkip = 4;         // calls that go straight to the full route after one that needed more
+
+// uniform complex entries in [-1, 1)^2: the SplitMix64 output function (Steele,
+// Lea & Flood 2014) of seed + i * golden gamma, 24 bits per component
+__global__ void sub_random_kernel(float2 *G, long long count, unsigned long long seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)i * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const float a = (float)(z >> 40) * (1.0f / 8388608.0f) - 1.0f;
+        const float b = (float)((z >> 16) & 0xFFFFFFull) * (1.0f / 8388608.0f) - 1.0f;
+        G[i] = make_float2(a, b);
+    }
+}
+
+__global__ void sub_widen_kernel(const float2 *B, long long count, double2 *B64) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 b = B[i];
+        B64[i] = make_double2((double)b.x, (double)b.y);
+    }
+}
+
+// part[block] = sum of |R_k|^2 over the block's grid-stride share (FP32 per
+// thread over 32 elements, FP64 across, fixed order)
+__global__ void __launch_bounds__(256) sub_frob_kernel(const float2 *R, long long count, double *part) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    float s = 0.0f;
+    int k = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 r = R[i];
+        s = fmaf(r.x, r.x, fmaf(r.y, r.y, s));
+        if (++k == 32) {
+            acc += (double)s;
+            s = 0.0f;
+            k = 0;
+        }
+    }
+    acc += (double)s;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// theta: the p ascending FP64 eigenvalues of C; lambda[0..n) = theta descending
+// (values below 0, FP64 rounding of zero ones, as 0) and zeros after, rescaled so
+// that they and the residual weight sum to |psi|^2 (FP64 norm partials, 4
+// doubles per CTA; the FP32 products leave a common relative deficit or excess
+// of order 1e-7); S = -sum lambda ln lambda; stats = {residual weight, sum of
+// lambda, values above 1e-12}.  A non-zero solver status or a non-finite value
+// makes S NaN.  One CTA.
+__global__ void __launch_bounds__(1024) sub_entropy_kernel(const double *theta, int p, const double *res_part,
+                                                           int nres, const double *norm_parts, int nnorm,
+                                                           const int *infos, int ninfo, int n, double *lambda,
+                                                           double *S, double *stats) {
+    __shared__ double red[32];
+    __shared__ double res_s, trace_s, scale_s;
+    int bad = 0;
+    if (threadIdx.x < 32) {
+        double t = 0.0, r = 0.0;
+        for (int b = threadIdx.x; b < nres; b += 32) r += res_part[b];
+        for (int b = threadIdx.x; b < nnorm; b += 32) t += norm_parts[4 * (size_t)b];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            r += __shfl_xor_sync(0xffffffffu, r, off);
+            t += __shfl_xor_sync(0xffffffffu, t, off);
+        }
+        if (threadIdx.x == 0) {
+            res_s = r;
+            trace_s = t;
+        }
+        if (!isfinite(r) || !isfinite(t)) bad = 1;
+        for (int q = threadIdx.x; q < ninfo; q += 32)
+            if (infos[q] != 0) bad = 1;
+    }
+    // sum of the captured values (fixed order)
+    double tot = 0.0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        const double l = theta[p - 1 - i];
+        if (!isfinite(l)) bad = 1;
+        if (l > 0.0) tot += l;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        const double want = trace_s - res_s;
+        scale_s = (t > 0.0 && want > 0.0) ? want / t : 1.0;
+    }
+    __syncthreads();
+    const double scale = scale_s;
+    double e = 0.0, cnt = 0.0;
+    tot = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double l = 0.0;
+        if (i < p) {
+            l = theta[p - 1 - i] * scale;
+            if (!(l > 0.0)) l = 0.0;
+        }
+        lambda[i] = l;
+        if (l > 0.0) {
+            e -= l * log(l);
+            tot += l;
+        }
+        if (l > 1e-12) cnt += 1.0;
+    }
+    double vals[3] = {e, tot, cnt};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) vals[q] += __shfl_xor_sync(0xffffffffu, vals[q], off);
+    }
+    for (int q = 0; q < 3; ++q) {
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vals[q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            vals[q] = t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *S = bad ? __longlong_as_double(0x7FF8000000000000ll) : vals[0];
+        stats[0] = res_s;
+        stats[1] = vals[1];
+        stats[2] = vals[2];
+    }
+}
+
+bool subspace_applicable(const Handle *h, int cut) {
+    const int L = h->L;
+    const int ls = cut < L - cut ? cut : L - cut;
+    const int n = 1 << ls;
+    return h->prec == OSMPS_MIXED && n >= 512 && n <= kRayMaxN;
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev) {
+    if (!subspace_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
+    const int L = h->L;
+    // M[x][k] = psi[x sx + k sk]: column-major n x K (sx = 1, ld n) or its
+    // transpose, column-major K x n (sk = 1, ld K)
+    const bool colM = cut > L - cut;
+    const int ls = colM ? L - cut : cut;
+    const int n = 1 << ls;
+    const int K = 1 << (L - ls);
+    std::lock_guard<std::mutex> lock(g_solver_mu);
+    if (!load_solver() || g_solver.params == nullptr || !g_solver.c_geqrf || !g_solver.c_ungqr ||
+        !g_solver.c_geqrf_bufsize || !g_solver.c_ungqr_bufsize || !load_blas())
+        return OSMPS_EUNSUPPORTED;
+    if (g_solver.set_stream(g_solver.handle, h->stream) != CUSOLVER_STATUS_SUCCESS ||
+        g_blas.set_stream(g_blas.handle, h->stream) != CUBLAS_STATUS_SUCCESS)
+        return OSMPS_ECUDA;
+    const cuComplex one = make_cuComplex(1.0f, 0.0f), zero = make_cuComplex(0.0f, 0.0f),
+                    mone = make_cuComplex(-1.0f, 0.0f);
+    cuComplex *A = (cuComplex *)const_cast<void *>(psi);
+    const double done = 1.0, dzero = 0.0;
+    // largest subspace worth trying: the FP64 eigenvalues of a p x p matrix cost
+    // about as much as the full FP32 route at p ~ 800 on this part
+    const int pmax = (n / 2 < kSubMaxP) ? n / 2 : kSubMaxP;
+    if (h->sub_skip > 0) {  // the last call needed more: the full route for a few calls
+        --h->sub_skip;
+        return OSMPS_ENOCONV;
+    }
+    int p = h->sub_hint > 0 ? h->sub_hint : 128;
+    p = ((p + 63) / 64) * 64;
+    if (p > pmax) p = pmax;
+    for (;;) {
+        // workspace sizes for this p (queries touch no memory)
+        int lw_qr = 0, lw_q = 0, lw_e = 0;
+        if (g_solver.c_geqrf_bufsize(g_solver.handle, n, p, A, n, &lw_qr) != CUSOLVER_STATUS_SUCCESS ||
+            g_solver.c_ungqr_bufsize(g_solver.handle, n, p, p, A, n, (const cuComplex *)A, &lw_q) !=
+                CUSOLVER_STATUS_SUCCESS ||
+            g_solver.z_bufsize(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, p,
+                               (const cuDoubleComplex *)A, p, (const double *)A, &lw_e) != CUSOLVER_STATUS_SUCCESS)
+            return OSMPS_ECUDA;
+        const size_t lw = (size_t)(lw_qr > lw_q ? lw_qr : lw_q);
+        const size_t o_Y = 0;
+        const size_t o_tau = o_Y + al256(sizeof(cuComplex) * (size_t)n * p);
+        const size_t o_B = o_tau + al256(sizeof(cuComplex) * (size_t)p);
+        const size_t o_B64 = o_B + al256(sizeof(cuComplex) * (size_t)p * K);  // also G (K x p) before B
+        const size_t o_C = o_B64 + al256(sizeof(cuDoubleComplex) * (size_t)p * K);
+        const size_t o_Mc = o_C + al256(sizeof(cuDoubleComplex) * (size_t)p * p);
+        const size_t o_th = o_Mc + al256(sizeof(cuComplex) * (size_t)n * K);
+        const size_t o_rp = o_th + al256(sizeof(double) * (size_t)p);
+        const size_t o_st = o_rp + al256(sizeof(double) * kSubResBlocks);
+        const size_t o_inf = o_st + al256(sizeof(double) * 4);
+        const size_t o_wq = o_inf + al256(sizeof(int) * 4);
+        const size_t o_we = o_wq + al256(sizeof(cuComplex) * (lw > 0 ? lw : 1));
+        const size_t need = o_we + al256(sizeof(cuDoubleComplex) * (size_t)(lw_e > 0 ? lw_e : 1));
+        CKS_(grow_ws(h, &h->sub_ws, &h->sub_ws_bytes, true, need));
+        char *ws = (char *)h->sub_ws;
+        cuComplex *Y = (cuComplex *)(ws + o_Y), *tau = (cuComplex *)(ws + o_tau), *B = (cuComplex *)(ws + o_B);
+        cuComplex *G = (cuComplex *)(ws + o_B64), *Mc = (cuComplex *)(ws + o_Mc);
+        cuDoubleComplex *B64 = (cuDoubleComplex *)(ws + o_B64), *C = (cuDoubleComplex *)(ws + o_C);
+        double *th = (double *)(ws + o_th), *rp = (double *)(ws + o_rp), *st = (double *)(ws + o_st);
+        int *inf = (int *)(ws + o_inf);
+        cuComplex *wq = (cuComplex *)(ws + o_wq);
+        cuDoubleComplex *we = (cuDoubleComplex *)(ws + o_we);
+        if (cudaMemsetAsync(inf, 0, sizeof(int) * 4, h->stream) != cudaSuccess) return OSMPS_ECUDA;
+        // G (K x p), Y = M G
+        sub_random_kernel<<<h->nsm * 4, 256, 0, h->stream>>>((float2 *)G, (long long)K * p, 0x5EEDull + (unsigned)p);
+        h->launches += 1;
+        cublasStatus_t bs =
+            colM ? g_blas.cgemm(g_blas.handle, CUBLAS_OP_N, CUBLAS_OP_N, n, p, K, &one, A, n, G, K, &zero, Y, n)
+                 : g_blas.cgemm(g_blas.handle, CUBLAS_OP_T, CUBLAS_OP_N, n, p, K, &one, A, K, G, K, &zero, Y, n);
+        if (bs != CUBLAS_STATUS_SUCCESS) return OSMPS_ECUDA;
+        // Q = orth(Y), in place
+        if (g_solver.c_geqrf(g_solver.handle, n, p, Y, n, tau, wq, (int)lw, inf) != CUSOLVER_STATUS_SUCCESS ||
+            g_solver.c_ungqr(g_solver.handle, n, p, p, Y, n, tau, wq, (int)lw, inf + 1) != CUSOLVER_STATUS_SUCCESS)
+            return OSMPS_ECUDA;
+        // B = Q^dag M (p x K)
+        bs = colM ? g_blas.cgemm(g_blas.handle, CUBLAS_OP_C, CUBLAS_OP_N, p, K, n, &one, Y, n, A, n, &zero, B, p)
+                  : g_blas.cgemm(g_blas.handle, CUBLAS_OP_C, CUBLAS_OP_T, p, K, n, &one, Y, n, A, K, &zero, B, p);
+        if (bs != CUBLAS_STATUS_SUCCESS) return OSMPS_ECUDA;
+        // C = B B^dag in FP64 (lower triangle) and its eigenvalues
+        sub_widen_kernel<<<h->nsm * 4, 256, 0, h->stream>>>((const float2 *)B, (long long)p * K, (double2 *)B64);
+        h->launches += 1;
+        if (g_blas.zherk(g_blas.handle, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, p, K, &done, B64, p, &dzero, C, p) !=
+            CUBLAS_STATUS_SUCCESS)
+            return OSMPS_ECUDA;
+        if (g_solver.z_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, p, C, p, th, we,
+                           lw_e, inf + 2) != CUSOLVER_STATUS_SUCCESS)
+            return OSMPS_ECUDA;
+        // the weight outside the subspace: |M - Q B|_F^2
+        if (cudaMemcpyAsync(Mc, A, sizeof(cuComplex) * (size_t)n * K, cudaMemcpyDeviceToDevice, h->stream) !=
+            cudaSuccess)
+            return OSMPS_ECUDA;
+        bs = colM ? g_blas.cgemm(g_blas.handle, CUBLAS_OP_N, CUBLAS_OP_N, n, K, p, &mone, Y, n, B, p, &one, Mc, n)
+                  : g_blas.cgemm(g_blas.handle, CUBLAS_OP_T, CUBLAS_OP_T, K, n, p, &mone, B, p, Y, n, &one, Mc, K);
+        if (bs != CUBLAS_STATUS_SUCCESS) return OSMPS_ECUDA;
+        sub_frob_kernel<<<kSubResBlocks, 256, 0, h->stream>>>((const float2 *)Mc, (long long)n * K, rp);
+        h->launches += 1;
+        int np = 0;
+        if (launch_norm2(h, psi, h->partials, &np) != cudaSuccess) return OSMPS_ECUDA;
+        sub_entropy_kernel<<<1, 1024, 0, h->stream>>>(th, p, rp, kSubResBlocks, h->partials, np, inf, 3, n, lambda_dev,
+                                                      S_dev, st);
+        h->launches += 1;
+        double hs[4] = {0, 0, 0, 0};
+        if (cudaMemcpyAsync(hs, st, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaMemcpyAsync(hs + 3, S_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return OSMPS_ECUDA;
+        if (!std::isfinite(hs[3])) return OSMPS_ENOCONV;  // solver status or a non-finite value
+        const double trace = hs[0] + hs[1];
+        if (hs[0] <= 1e-9 * trace) {
+            // the next call starts from the values that mattered here, plus a quarter and 64
+            const int cnt = (int)hs[2];
+            h->sub_hint = cnt + cnt / 4 + 64;
+            return OSMPS_OK;
+        }
+        if (p >= pmax) {
+            h->sub_hint = pmax;
+            h->sub_skip = kSubSkip;
+            return OSMPS_ENOCONV;  // too much weight outside any affordable subspace: the full route
+        }
+        p = 2 * p < pmax ? 2 * p : pmax;
+    }
 }
 
 }  // namespace osmps
