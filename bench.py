@@ -216,6 +216,13 @@ def run_arm(args, prec, steps, warmup, world, e2e=True):
         keep(step(psi))
     chain.measure_wait()
     torch.cuda.synchronize()
+    if e2e:
+        # the state where the timed steps start: the end-to-end leg repeats the same
+        # stretch of the trajectory (the cost of a measurement depends on how many
+        # Schmidt values matter, which grows along it)
+        host_start = torch.empty(D, dtype=chain.dtype, pin_memory=True)
+        chain.download(host_start, psi)
+        torch.cuda.synchronize()
     launches0 = chain_launches(chain)
     chain.timing_read(reset=True)
     chain.timing_enable(True)
@@ -248,8 +255,7 @@ def run_arm(args, prec, steps, warmup, world, e2e=True):
            "t_end": (warmup + steps) * SIM_TIME_PER_STEP, "psi_final": psi.cpu()}
     # end to end through the public API with host buffers
     if e2e:
-        host = torch.empty(D, dtype=chain.dtype, pin_memory=True)
-        chain.download(host, psi)
+        host = host_start
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(steps):
