@@ -534,8 +534,8 @@ static bool load_solver() {
     return true;
 }
 
-// cuBLAS, loaded at first use like the solver: complex FP32 GEMM (default math
-// mode: FP32 arithmetic, no TF32) and the FP64 Hermitian rank-k update
+// cuBLAS, loaded at first use like the solver; only complex FP32 GEMM is used
+// (default math mode: FP32 arithmetic, no TF32)
 struct BlasLib {
     bool tried = false;
     bool ok = false;
@@ -544,7 +544,6 @@ struct BlasLib {
     decltype(&cublasCreate_v2) create = nullptr;
     decltype(&cublasSetStream_v2) set_stream = nullptr;
     decltype(&cublasCgemm_v2) cgemm = nullptr;
-    decltype(&cublasZherk_v2) zherk = nullptr;
 };
 static BlasLib g_blas;
 
@@ -560,8 +559,7 @@ static bool load_blas() {
     g_blas.create = (decltype(g_blas.create))dlsym(g_blas.so, "cublasCreate_v2");
     g_blas.set_stream = (decltype(g_blas.set_stream))dlsym(g_blas.so, "cublasSetStream_v2");
     g_blas.cgemm = (decltype(g_blas.cgemm))dlsym(g_blas.so, "cublasCgemm_v2");
-    g_blas.zherk = (decltype(g_blas.zherk))dlsym(g_blas.so, "cublasZherk_v2");
-    if (!g_blas.create || !g_blas.set_stream || !g_blas.cgemm || !g_blas.zherk) return false;
+    if (!g_blas.create || !g_blas.set_stream || !g_blas.cgemm) return false;
     if (g_blas.create(&g_blas.handle) != CUBLAS_STATUS_SUCCESS) return false;
     g_blas.ok = true;
     return true;
@@ -1059,8 +1057,8 @@ osmps_status schmidt_rayleigh(Handle *h, const void *psi, int cut, void *rho, do
 // the L = 24 quench to t = 2.5); the rest carry < 1e-8 of weight.  With M the
 // n x K block matrix of psi and G a K x p random block: Y = M G, Q = orth(Y)
 // (Householder), B = Q^dag M (FP32 GEMMs); the Schmidt values are the squared
-// singular values of B, taken as the eigenvalues of C = B B^dag formed and
-// diagonalised in FP64 (the FP32 products are exact there, so no value is lost
+// singular values of B, taken as the eigenvalues of C = B B^dag formed (own
+// split-K kernel) and diagonalised in FP64 (the FP32 products are exact there, so no value is lost
 // to squaring: each keeps the error 2 sigma |dB| of the singular-value route).
 // The weight left outside the subspace, |M - Q B|_F^2, is measured directly
 // (not by subtraction from the trace) and must stay at or below 1e-9 of the
@@ -1085,11 +1083,80 @@ __global__ void sub_random_kernel(float2 *G, long long count, unsigned long long
     }
 }
 
-__global__ void sub_widen_kernel(const float2 *B, long long count, double2 *B64) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float2 b = B[i];
-        B64[i] = make_double2((double)b.x, (double)b.y);
+// C = B B^dag in FP64 from the FP32 B (column-major p x K): the products of FP32
+// values are exact in FP64.  One CTA per 32 x 32 tile of the lower triangle and
+// per chunk of K (split so the grid fills the GPU), the chunk of both row
+// blocks staged in shared memory as FP64; partial tiles to part[split], summed
+// in a fixed order by sub_gram_sum_kernel.
+constexpr int kG64T = 32;   // tile edge
+constexpr int kG64K = 32;   // K staged per step (2 x 16 KB of FP64 in shared memory)
+__global__ void __launch_bounds__(256) sub_gram64_kernel(const float2 *B, int p, long long K, int nsplit,
+                                                         double2 *part) {
+    __shared__ double2 As[kG64K][kG64T], Bs[kG64K][kG64T];
+    // lower-triangle tile index -> (ti, tj), ti >= tj
+    int t = blockIdx.x, ti = 0;
+    while (t > ti) {
+        t -= ti + 1;
+        ++ti;
+    }
+    const int tj = t;
+    const int split = blockIdx.y;
+    const long long k0 = K * split / nsplit, k1 = K * (split + 1) / nsplit;
+    const int r = threadIdx.x & 31, c0 = threadIdx.x >> 5;  // rows r, columns c0 + 8 m
+    double cr[4] = {0, 0, 0, 0}, ci[4] = {0, 0, 0, 0};
+    for (long long kb = k0; kb < k1; kb += kG64K) {
+        const int kn = (int)((k1 - kb) < kG64K ? (k1 - kb) : kG64K);
+        for (int e = threadIdx.x; e < kG64K * kG64T; e += 256) {
+            const int kk = e / kG64T, ii = e % kG64T;
+            double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+            if (kk < kn) {
+                const int ia = ti * kG64T + ii, ib = tj * kG64T + ii;
+                if (ia < p) {
+                    const float2 v = B[(size_t)ia + (size_t)(kb + kk) * p];
+                    a = make_double2((double)v.x, (double)v.y);
+                }
+                if (ib < p) {
+                    const float2 v = B[(size_t)ib + (size_t)(kb + kk) * p];
+                    b = make_double2((double)v.x, (double)v.y);
+                }
+            }
+            As[kk][ii] = a;
+            Bs[kk][ii] = b;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kn; ++kk) {
+            const double2 a = As[kk][r];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const double2 b = Bs[kk][c0 + 8 * m];
+                // a conj(b)
+                cr[m] = fma(a.x, b.x, fma(a.y, b.y, cr[m]));
+                ci[m] = fma(a.y, b.x, fma(-a.x, b.y, ci[m]));
+            }
+        }
+        __syncthreads();
+    }
+    const int i = ti * kG64T + r;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int j = tj * kG64T + c0 + 8 * m;
+        if (i < p && j < p) part[(size_t)split * p * p + (size_t)i + (size_t)j * p] = make_double2(cr[m], ci[m]);
+    }
+}
+// C[i + j p] = sum over splits (fixed order) for i >= j
+__global__ void sub_gram_sum_kernel(const double2 *part, int p, int nsplit, double2 *C) {
+    const long long total = (long long)p * p;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % p), j = (int)(e / p);
+        if (i < j) continue;
+        double2 s = make_double2(0.0, 0.0);
+        for (int q = 0; q < nsplit; ++q) {
+            const double2 v = part[(size_t)q * total + e];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        C[e] = s;
     }
 }
 
@@ -1239,7 +1306,6 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
     const cuComplex one = make_cuComplex(1.0f, 0.0f), zero = make_cuComplex(0.0f, 0.0f),
                     mone = make_cuComplex(-1.0f, 0.0f);
     cuComplex *A = (cuComplex *)const_cast<void *>(psi);
-    const double done = 1.0, dzero = 0.0;
     // largest subspace worth trying: the FP64 eigenvalues of a p x p matrix cost
     // about as much as the full FP32 route at p ~ 800 on this part
     const int pmax = (n / 2 < kSubMaxP) ? n / 2 : kSubMaxP;
@@ -1263,8 +1329,15 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
         const size_t o_Y = 0;
         const size_t o_tau = o_Y + al256(sizeof(cuComplex) * (size_t)n * p);
         const size_t o_B = o_tau + al256(sizeof(cuComplex) * (size_t)p);
-        const size_t o_B64 = o_B + al256(sizeof(cuComplex) * (size_t)p * K);  // also G (K x p) before B
-        const size_t o_C = o_B64 + al256(sizeof(cuDoubleComplex) * (size_t)p * K);
+        // lower-triangle tiles of C and the K split that fills the GPU
+        const int nt = (p + kG64T - 1) / kG64T, ntl = nt * (nt + 1) / 2;
+        int nsplit = (2 * h->nsm + ntl - 1) / ntl;
+        if (nsplit > 16) nsplit = 16;
+        if (nsplit < 1) nsplit = 1;
+        const size_t gpart = sizeof(cuDoubleComplex) * (size_t)nsplit * p * p;
+        const size_t gk = sizeof(cuComplex) * (size_t)p * K;  // G (K x p) before B
+        const size_t o_GP = o_B + al256(sizeof(cuComplex) * (size_t)p * K);  // G, then the Gram partials
+        const size_t o_C = o_GP + al256(gpart > gk ? gpart : gk);
         const size_t o_Mc = o_C + al256(sizeof(cuDoubleComplex) * (size_t)p * p);
         const size_t o_th = o_Mc + al256(sizeof(cuComplex) * (size_t)n * K);
         const size_t o_rp = o_th + al256(sizeof(double) * (size_t)p);
@@ -1276,8 +1349,8 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
         CKS_(grow_ws(h, &h->sub_ws, &h->sub_ws_bytes, true, need));
         char *ws = (char *)h->sub_ws;
         cuComplex *Y = (cuComplex *)(ws + o_Y), *tau = (cuComplex *)(ws + o_tau), *B = (cuComplex *)(ws + o_B);
-        cuComplex *G = (cuComplex *)(ws + o_B64), *Mc = (cuComplex *)(ws + o_Mc);
-        cuDoubleComplex *B64 = (cuDoubleComplex *)(ws + o_B64), *C = (cuDoubleComplex *)(ws + o_C);
+        cuComplex *G = (cuComplex *)(ws + o_GP), *Mc = (cuComplex *)(ws + o_Mc);
+        cuDoubleComplex *GP = (cuDoubleComplex *)(ws + o_GP), *C = (cuDoubleComplex *)(ws + o_C);
         double *th = (double *)(ws + o_th), *rp = (double *)(ws + o_rp), *st = (double *)(ws + o_st);
         int *inf = (int *)(ws + o_inf);
         cuComplex *wq = (cuComplex *)(ws + o_wq);
@@ -1299,11 +1372,10 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
                   : g_blas.cgemm(g_blas.handle, CUBLAS_OP_C, CUBLAS_OP_T, p, K, n, &one, Y, n, A, K, &zero, B, p);
         if (bs != CUBLAS_STATUS_SUCCESS) return OSMPS_ECUDA;
         // C = B B^dag in FP64 (lower triangle) and its eigenvalues
-        sub_widen_kernel<<<h->nsm * 4, 256, 0, h->stream>>>((const float2 *)B, (long long)p * K, (double2 *)B64);
-        h->launches += 1;
-        if (g_blas.zherk(g_blas.handle, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, p, K, &done, B64, p, &dzero, C, p) !=
-            CUBLAS_STATUS_SUCCESS)
-            return OSMPS_ECUDA;
+        sub_gram64_kernel<<<dim3((unsigned)ntl, (unsigned)nsplit), 256, 0, h->stream>>>((const float2 *)B, p, (long long)K,
+                                                                                        nsplit, (double2 *)GP);
+        sub_gram_sum_kernel<<<h->nsm * 4, 256, 0, h->stream>>>((const double2 *)GP, p, nsplit, (double2 *)C);
+        h->launches += 2;
         if (g_solver.z_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, p, C, p, th, we,
                            lw_e, inf + 2) != CUSOLVER_STATUS_SUCCESS)
             return OSMPS_ECUDA;
