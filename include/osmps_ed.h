@@ -142,22 +142,26 @@ osmps_status osmps_ed_set_sm_count(osmps_ed_t *ed, int nsm);
  *      Falls back to 1 when the library eigen-solver fails or its eigenvectors
  *      give a non-finite value (seen for nearly product states whose rho has
  *      FP32-subnormal entries).  EUNSUPPORTED where it does not apply.
- *   3  automatic (the default): complex128 takes 0 (FP64 Gram and eigenvalues
- *      meet 1e-10); complex64 takes 4 where it applies, else 2 where that
+ *   3  automatic (the default): 4 where it applies; else complex128 takes 0
+ *      (FP64 Gram and eigenvalues meet 1e-10) and complex64 takes 2 where it
  *      applies, else 1 for blocks up to 8192 rows, else 0.
- *   4  dominant subspace (complex64 only; 512 <= 2^min(cut, L-cut) <= 8192):
- *      Y = M G for a seeded random K x p block G, Q = orth(Y) (Householder),
- *      B = Q^dag M, W the eigenvectors of B B^dag (p x p), and the Schmidt
- *      values as Rayleigh quotients |w_i^dag B|^2 (library complex FP32 GEMMs,
- *      QR and eigen-solver, sums in FP64).  The weight outside the subspace,
- *      |M - Q B|_F^2, is measured directly and must stay at or below 1e-9 of
- *      the trace (its share of S is then < 1e-7); otherwise p doubles, and past
- *      n/2 (or on a non-finite value) the call takes method 2, then 1.  p starts
- *      at twice the number of values above 1e-12 at the handle's previous call
- *      (128 the first time).  The spectrum has p values and zeros after them.
- *      Scratch (Y, B, W, Z: 2 n p + 2 p K + p^2 complex, a copy of M, solver
- *      work) is kept by the handle.  The cost follows p: weakly entangled
- *      states (p ~ 100) need a small fraction of the full eigen-solve.
+ *   4  dominant subspace (512 <= 2^min(cut, L-cut) <= 8192): Y = M G for a
+ *      seeded random K x p block G, Q = orth(Y) (library Householder QR),
+ *      B = Q^dag M (library GEMMs in the handle's precision), and the Schmidt
+ *      values as the eigenvalues of C = B B^dag formed and diagonalised in FP64
+ *      (the squared singular values of B), rescaled with the residual weight to
+ *      the FP64 norm.  The weight outside the subspace, |M - Q B|_F^2, is
+ *      measured directly and must stay at or below 1e-9 (complex64) or 2e-12
+ *      (complex128) of the trace, its share of S then below the precision's
+ *      tolerance; otherwise p doubles up to min(n/2, 768), beyond which (or on a
+ *      non-finite value) the call takes the full route (complex64: method 2,
+ *      then 1; complex128: method 0) and skips the subspace for four calls.  p
+ *      starts from the number of values above 1e-12 at the handle's previous
+ *      call plus a quarter and 64 (128 the first time).  The spectrum has p
+ *      values and zeros after them.  Scratch (n p + 2 p K complex, up to
+ *      16 p^2 FP64 complex partials, a copy of M, solver work) is kept by the
+ *      handle.  The cost follows p: weakly entangled states (p ~ 100) need a
+ *      small fraction of the full eigen-solve.
  * osmps_ed_schmidt_entropy_async takes method 0 (also when 3 is set) and
  * returns EUNSUPPORTED for 1, 2 and 4. */
 osmps_status osmps_ed_set_entropy_method(osmps_ed_t *ed, int method);

@@ -1060,10 +1060,10 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
     const size_t gbytes = (size_t)n * n * h->esize;
     int method = h->entropy_method;
     if (method == ENT_AUTO) {
-        if (h->prec == OSMPS_FP64)
-            method = ENT_GRAM;
-        else if (subspace_applicable(h, cut))
+        if (subspace_applicable(h, cut))
             method = ENT_SUBSPACE;
+        else if (h->prec == OSMPS_FP64)
+            method = ENT_GRAM;
         else
             method = rayleigh_applicable(h, cut) ? ENT_RAYLEIGH : (n <= 8192 ? ENT_SVD : ENT_GRAM);
     }
@@ -1088,7 +1088,8 @@ osmps_status osmps_ed_schmidt_entropy(osmps_ed_t *ed, const void *psi, int cut, 
             return OSMPS_OK;
         }
         if (rs != OSMPS_ENOCONV && rs != OSMPS_EUNSUPPORTED) return rs;
-        method = rayleigh_applicable(h, cut) ? ENT_RAYLEIGH : ENT_SVD;  // the full route
+        // the full route
+        method = h->prec == OSMPS_FP64 ? ENT_GRAM : (rayleigh_applicable(h, cut) ? ENT_RAYLEIGH : ENT_SVD);
     }
     if (method == ENT_RAYLEIGH && !rayleigh_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
     if (method == ENT_RAYLEIGH) {

@@ -134,9 +134,10 @@ osmps_status schmidt_svd(Handle *h, const void *psi, int cut, double *lambda_dev
 // OSMPS_ENOCONV when the library eigen-solver failed (callers then take schmidt_svd)
 bool rayleigh_applicable(const Handle *h, int cut);
 osmps_status schmidt_rayleigh(Handle *h, const void *psi, int cut, void *rho, double *lambda_dev, double *S_dev);
-// Schmidt values from the dominant subspace (complex64, 512 <= n <= 8192): OK, or
-// ENOCONV when the weight outside an affordable subspace stays above 1e-9 of the
-// trace or a value is not finite (the caller then takes the full route)
+// Schmidt values from the dominant subspace (512 <= n <= 8192): OK, or ENOCONV when
+// the weight outside an affordable subspace stays above 1e-9 (complex64) or
+// 2e-12 (complex128) of the trace or a value is not finite (the caller then takes
+// the full route)
 bool subspace_applicable(const Handle *h, int cut);
 osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev);
 bool rayleigh_tc_supported(int n, long long K);
@@ -148,9 +149,9 @@ enum EntropyMethod : int {
     ENT_GRAM = 0,      // eigenvalues of the Gram product
     ENT_SVD = 1,       // squared singular values of M
     ENT_RAYLEIGH = 2,  // Rayleigh quotients of the Gram product's eigenvectors (complex64)
-    ENT_AUTO = 3,      // complex64: subspace, else Rayleigh where they apply, else singular values up to
-                       // 2^13 rows, else Gram; complex128: Gram
-    ENT_SUBSPACE = 4   // Rayleigh quotients on the dominant subspace (complex64), full route as fallback
+    ENT_AUTO = 3,      // subspace where it applies; else complex64: Rayleigh where it applies, else
+                       // singular values up to 2^13 rows, else Gram; complex128: Gram
+    ENT_SUBSPACE = 4   // squared singular values on the dominant subspace, full route as fallback
 };
 // S and the descending spectrum from ascending FP64 eigenvalues w (n values) on a stream
 cudaError_t launch_entropy(cudaStream_t stream, const double *w, int n, double *lambda_dev, double *S_dev);

@@ -494,6 +494,10 @@ struct SolverLib {
     decltype(&cusolverDnCgeqrf) c_geqrf = nullptr;
     decltype(&cusolverDnCungqr_bufferSize) c_ungqr_bufsize = nullptr;
     decltype(&cusolverDnCungqr) c_ungqr = nullptr;
+    decltype(&cusolverDnZgeqrf_bufferSize) z_geqrf_bufsize = nullptr;
+    decltype(&cusolverDnZgeqrf) z_geqrf = nullptr;
+    decltype(&cusolverDnZungqr_bufferSize) z_ungqr_bufsize = nullptr;
+    decltype(&cusolverDnZungqr) z_ungqr = nullptr;
     cusolverDnParams_t params = nullptr;  // default options, read-only after creation
 };
 static SolverLib g_solver;
@@ -530,12 +534,16 @@ static bool load_solver() {
     g_solver.c_geqrf = (decltype(g_solver.c_geqrf))dlsym(g_solver.so, "cusolverDnCgeqrf");
     g_solver.c_ungqr_bufsize = (decltype(g_solver.c_ungqr_bufsize))dlsym(g_solver.so, "cusolverDnCungqr_bufferSize");
     g_solver.c_ungqr = (decltype(g_solver.c_ungqr))dlsym(g_solver.so, "cusolverDnCungqr");
+    g_solver.z_geqrf_bufsize = (decltype(g_solver.z_geqrf_bufsize))dlsym(g_solver.so, "cusolverDnZgeqrf_bufferSize");
+    g_solver.z_geqrf = (decltype(g_solver.z_geqrf))dlsym(g_solver.so, "cusolverDnZgeqrf");
+    g_solver.z_ungqr_bufsize = (decltype(g_solver.z_ungqr_bufsize))dlsym(g_solver.so, "cusolverDnZungqr_bufferSize");
+    g_solver.z_ungqr = (decltype(g_solver.z_ungqr))dlsym(g_solver.so, "cusolverDnZungqr");
     g_solver.ok = true;
     return true;
 }
 
-// cuBLAS, loaded at first use like the solver; only complex FP32 GEMM is used
-// (default math mode: FP32 arithmetic, no TF32)
+// cuBLAS, loaded at first use like the solver; only complex GEMM is used
+// (default math mode: FP32 or FP64 arithmetic as named, no TF32)
 struct BlasLib {
     bool tried = false;
     bool ok = false;
@@ -544,6 +552,7 @@ struct BlasLib {
     decltype(&cublasCreate_v2) create = nullptr;
     decltype(&cublasSetStream_v2) set_stream = nullptr;
     decltype(&cublasCgemm_v2) cgemm = nullptr;
+    decltype(&cublasZgemm_v2) zgemm = nullptr;
 };
 static BlasLib g_blas;
 
@@ -559,7 +568,8 @@ static bool load_blas() {
     g_blas.create = (decltype(g_blas.create))dlsym(g_blas.so, "cublasCreate_v2");
     g_blas.set_stream = (decltype(g_blas.set_stream))dlsym(g_blas.so, "cublasSetStream_v2");
     g_blas.cgemm = (decltype(g_blas.cgemm))dlsym(g_blas.so, "cublasCgemm_v2");
-    if (!g_blas.create || !g_blas.set_stream || !g_blas.cgemm) return false;
+    g_blas.zgemm = (decltype(g_blas.zgemm))dlsym(g_blas.so, "cublasZgemm_v2");
+    if (!g_blas.create || !g_blas.set_stream || !g_blas.cgemm || !g_blas.zgemm) return false;
     if (g_blas.create(&g_blas.handle) != CUBLAS_STATUS_SUCCESS) return false;
     g_blas.ok = true;
     return true;
@@ -1070,7 +1080,8 @@ constexpr int kSubSkip = 4;         // calls that go straight to the full route 
 
 // uniform complex entries in [-1, 1)^2: the SplitMix64 output function (Steele,
 // Lea & Flood 2014) of seed + i * golden gamma, 24 bits per component
-__global__ void sub_random_kernel(float2 *G, long long count, unsigned long long seed) {
+template <typename V2>
+__global__ void sub_random_kernel(V2 *G, long long count, unsigned long long seed) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x) {
         unsigned long long z = seed + (unsigned long long)i * 0x9E3779B97F4A7C15ull;
@@ -1079,18 +1090,22 @@ __global__ void sub_random_kernel(float2 *G, long long count, unsigned long long
         z ^= z >> 31;
         const float a = (float)(z >> 40) * (1.0f / 8388608.0f) - 1.0f;
         const float b = (float)((z >> 16) & 0xFFFFFFull) * (1.0f / 8388608.0f) - 1.0f;
-        G[i] = make_float2(a, b);
+        G[i].x = a;
+        G[i].y = b;
     }
 }
+__device__ __forceinline__ double2 to_d2(const float2 v) { return make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ double2 to_d2(const double2 v) { return v; }
 
-// C = B B^dag in FP64 from the FP32 B (column-major p x K): the products of FP32
-// values are exact in FP64.  One CTA per 32 x 32 tile of the lower triangle and
+// C = B B^dag in FP64 from B (column-major p x K, FP32 or FP64): the products of
+// FP32 values are exact in FP64.  One CTA per 32 x 32 tile of the lower triangle and
 // per chunk of K (split so the grid fills the GPU), the chunk of both row
 // blocks staged in shared memory as FP64; partial tiles to part[split], summed
 // in a fixed order by sub_gram_sum_kernel.
 constexpr int kG64T = 32;   // tile edge
 constexpr int kG64K = 32;   // K staged per step (2 x 16 KB of FP64 in shared memory)
-__global__ void __launch_bounds__(256) sub_gram64_kernel(const float2 *B, int p, long long K, int nsplit,
+template <typename V2>
+__global__ void __launch_bounds__(256) sub_gram64_kernel(const V2 *B, int p, long long K, int nsplit,
                                                          double2 *part) {
     __shared__ double2 As[kG64K][kG64T], Bs[kG64K][kG64T];
     // lower-triangle tile index -> (ti, tj), ti >= tj
@@ -1111,14 +1126,8 @@ __global__ void __launch_bounds__(256) sub_gram64_kernel(const float2 *B, int p,
             double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
             if (kk < kn) {
                 const int ia = ti * kG64T + ii, ib = tj * kG64T + ii;
-                if (ia < p) {
-                    const float2 v = B[(size_t)ia + (size_t)(kb + kk) * p];
-                    a = make_double2((double)v.x, (double)v.y);
-                }
-                if (ib < p) {
-                    const float2 v = B[(size_t)ib + (size_t)(kb + kk) * p];
-                    b = make_double2((double)v.x, (double)v.y);
-                }
+                if (ia < p) a = to_d2(B[(size_t)ia + (size_t)(kb + kk) * p]);
+                if (ib < p) b = to_d2(B[(size_t)ib + (size_t)(kb + kk) * p]);
             }
             As[kk][ii] = a;
             Bs[kk][ii] = b;
@@ -1160,20 +1169,22 @@ __global__ void sub_gram_sum_kernel(const double2 *part, int p, int nsplit, doub
     }
 }
 
-// part[block] = sum of |R_k|^2 over the block's grid-stride share (FP32 per
-// thread over 32 elements, FP64 across, fixed order)
-__global__ void __launch_bounds__(256) sub_frob_kernel(const float2 *R, long long count, double *part) {
+// part[block] = sum of |R_k|^2 over the block's grid-stride share (in the
+// element type per thread over 32 elements, FP64 across, fixed order)
+template <typename V2>
+__global__ void __launch_bounds__(256) sub_frob_kernel(const V2 *R, long long count, double *part) {
+    typedef decltype(R->x) E;
     __shared__ double red[8];
     double acc = 0.0;
-    float s = 0.0f;
+    E s = 0;
     int k = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x) {
-        const float2 r = R[i];
-        s = fmaf(r.x, r.x, fmaf(r.y, r.y, s));
+        const V2 r = R[i];
+        s = fma(r.x, r.x, fma(r.y, r.y, s));
         if (++k == 32) {
             acc += (double)s;
-            s = 0.0f;
+            s = 0;
             k = 0;
         }
     }
@@ -1282,13 +1293,71 @@ bool subspace_applicable(const Handle *h, int cut) {
     const int L = h->L;
     const int ls = cut < L - cut ? cut : L - cut;
     const int n = 1 << ls;
-    return h->prec == OSMPS_MIXED && n >= 512 && n <= kRayMaxN;
+    return n >= 512 && n <= kRayMaxN;
 }
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev) {
-    if (!subspace_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
+// library entry points of the route per precision; the residual bound keeps the
+// uncaptured share of S below the precision's tolerance (1e-5 and 1e-10):
+// w (1 + ln(n / w)) < 1e-7 for w = 1e-9, < 1e-10 for w = 2e-12
+template <typename T> struct SubLib;
+template <> struct SubLib<float> {
+    typedef cuComplex C;
+    typedef float2 V2;
+    static constexpr double kResTol = 1e-9;
+    static bool loaded() {
+        return g_solver.c_geqrf && g_solver.c_ungqr && g_solver.c_geqrf_bufsize && g_solver.c_ungqr_bufsize;
+    }
+    static C scal(float r) { return make_cuComplex(r, 0.0f); }
+    static cublasStatus_t gemm(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const C *al,
+                               const C *A, int lda, const C *B, int ldb, const C *be, C *Cm, int ldc) {
+        return g_blas.cgemm(g_blas.handle, ta, tb, m, n, k, al, A, lda, B, ldb, be, Cm, ldc);
+    }
+    static bool qr_sizes(int m, int n, C *A, int *lw) {
+        int a = 0, b = 0;
+        if (g_solver.c_geqrf_bufsize(g_solver.handle, m, n, A, m, &a) != CUSOLVER_STATUS_SUCCESS ||
+            g_solver.c_ungqr_bufsize(g_solver.handle, m, n, n, A, m, A, &b) != CUSOLVER_STATUS_SUCCESS)
+            return false;
+        *lw = a > b ? a : b;
+        return true;
+    }
+    static bool qr(int m, int n, C *A, C *tau, C *w, int lw, int *info) {
+        return g_solver.c_geqrf(g_solver.handle, m, n, A, m, tau, w, lw, info) == CUSOLVER_STATUS_SUCCESS &&
+               g_solver.c_ungqr(g_solver.handle, m, n, n, A, m, tau, w, lw, info + 1) == CUSOLVER_STATUS_SUCCESS;
+    }
+};
+template <> struct SubLib<double> {
+    typedef cuDoubleComplex C;
+    typedef double2 V2;
+    static constexpr double kResTol = 2e-12;
+    static bool loaded() {
+        return g_solver.z_geqrf && g_solver.z_ungqr && g_solver.z_geqrf_bufsize && g_solver.z_ungqr_bufsize;
+    }
+    static C scal(double r) { return make_cuDoubleComplex(r, 0.0); }
+    static cublasStatus_t gemm(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const C *al,
+                               const C *A, int lda, const C *B, int ldb, const C *be, C *Cm, int ldc) {
+        return g_blas.zgemm(g_blas.handle, ta, tb, m, n, k, al, A, lda, B, ldb, be, Cm, ldc);
+    }
+    static bool qr_sizes(int m, int n, C *A, int *lw) {
+        int a = 0, b = 0;
+        if (g_solver.z_geqrf_bufsize(g_solver.handle, m, n, A, m, &a) != CUSOLVER_STATUS_SUCCESS ||
+            g_solver.z_ungqr_bufsize(g_solver.handle, m, n, n, A, m, A, &b) != CUSOLVER_STATUS_SUCCESS)
+            return false;
+        *lw = a > b ? a : b;
+        return true;
+    }
+    static bool qr(int m, int n, C *A, C *tau, C *w, int lw, int *info) {
+        return g_solver.z_geqrf(g_solver.handle, m, n, A, m, tau, w, lw, info) == CUSOLVER_STATUS_SUCCESS &&
+               g_solver.z_ungqr(g_solver.handle, m, n, n, A, m, tau, w, lw, info + 1) == CUSOLVER_STATUS_SUCCESS;
+    }
+};
+
+template <typename T>
+static osmps_status schmidt_subspace_t(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev) {
+    typedef SubLib<T> Lib;
+    typedef typename Lib::C C;
+    typedef typename Lib::V2 V2;
     const int L = h->L;
     // M[x][k] = psi[x sx + k sk]: column-major n x K (sx = 1, ld n) or its
     // transpose, column-major K x n (sk = 1, ld K)
@@ -1297,15 +1366,12 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
     const int n = 1 << ls;
     const int K = 1 << (L - ls);
     std::lock_guard<std::mutex> lock(g_solver_mu);
-    if (!load_solver() || g_solver.params == nullptr || !g_solver.c_geqrf || !g_solver.c_ungqr ||
-        !g_solver.c_geqrf_bufsize || !g_solver.c_ungqr_bufsize || !load_blas())
-        return OSMPS_EUNSUPPORTED;
+    if (!load_solver() || !Lib::loaded() || !load_blas()) return OSMPS_EUNSUPPORTED;
     if (g_solver.set_stream(g_solver.handle, h->stream) != CUSOLVER_STATUS_SUCCESS ||
         g_blas.set_stream(g_blas.handle, h->stream) != CUBLAS_STATUS_SUCCESS)
         return OSMPS_ECUDA;
-    const cuComplex one = make_cuComplex(1.0f, 0.0f), zero = make_cuComplex(0.0f, 0.0f),
-                    mone = make_cuComplex(-1.0f, 0.0f);
-    cuComplex *A = (cuComplex *)const_cast<void *>(psi);
+    const C one = Lib::scal(1), zero = Lib::scal(0), mone = Lib::scal(-1);
+    C *A = (C *)const_cast<void *>(psi);
     // largest subspace worth trying: the FP64 eigenvalues of a p x p matrix cost
     // about as much as the full FP32 route at p ~ 800 on this part
     const int pmax = (n / 2 < kSubMaxP) ? n / 2 : kSubMaxP;
@@ -1318,75 +1384,69 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
     if (p > pmax) p = pmax;
     for (;;) {
         // workspace sizes for this p (queries touch no memory)
-        int lw_qr = 0, lw_q = 0, lw_e = 0;
-        if (g_solver.c_geqrf_bufsize(g_solver.handle, n, p, A, n, &lw_qr) != CUSOLVER_STATUS_SUCCESS ||
-            g_solver.c_ungqr_bufsize(g_solver.handle, n, p, p, A, n, (const cuComplex *)A, &lw_q) !=
-                CUSOLVER_STATUS_SUCCESS ||
+        int lw = 0, lw_e = 0;
+        if (!Lib::qr_sizes(n, p, A, &lw) ||
             g_solver.z_bufsize(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, p,
                                (const cuDoubleComplex *)A, p, (const double *)A, &lw_e) != CUSOLVER_STATUS_SUCCESS)
             return OSMPS_ECUDA;
-        const size_t lw = (size_t)(lw_qr > lw_q ? lw_qr : lw_q);
-        const size_t o_Y = 0;
-        const size_t o_tau = o_Y + al256(sizeof(cuComplex) * (size_t)n * p);
-        const size_t o_B = o_tau + al256(sizeof(cuComplex) * (size_t)p);
         // lower-triangle tiles of C and the K split that fills the GPU
         const int nt = (p + kG64T - 1) / kG64T, ntl = nt * (nt + 1) / 2;
         int nsplit = (2 * h->nsm + ntl - 1) / ntl;
         if (nsplit > 16) nsplit = 16;
         if (nsplit < 1) nsplit = 1;
         const size_t gpart = sizeof(cuDoubleComplex) * (size_t)nsplit * p * p;
-        const size_t gk = sizeof(cuComplex) * (size_t)p * K;  // G (K x p) before B
-        const size_t o_GP = o_B + al256(sizeof(cuComplex) * (size_t)p * K);  // G, then the Gram partials
+        const size_t gk = sizeof(C) * (size_t)p * K;  // G (K x p) before B
+        const size_t o_Y = 0;
+        const size_t o_tau = o_Y + al256(sizeof(C) * (size_t)n * p);
+        const size_t o_B = o_tau + al256(sizeof(C) * (size_t)p);
+        const size_t o_GP = o_B + al256(sizeof(C) * (size_t)p * K);  // G, then the Gram partials
         const size_t o_C = o_GP + al256(gpart > gk ? gpart : gk);
         const size_t o_Mc = o_C + al256(sizeof(cuDoubleComplex) * (size_t)p * p);
-        const size_t o_th = o_Mc + al256(sizeof(cuComplex) * (size_t)n * K);
+        const size_t o_th = o_Mc + al256(sizeof(C) * (size_t)n * K);
         const size_t o_rp = o_th + al256(sizeof(double) * (size_t)p);
         const size_t o_st = o_rp + al256(sizeof(double) * kSubResBlocks);
         const size_t o_inf = o_st + al256(sizeof(double) * 4);
         const size_t o_wq = o_inf + al256(sizeof(int) * 4);
-        const size_t o_we = o_wq + al256(sizeof(cuComplex) * (lw > 0 ? lw : 1));
+        const size_t o_we = o_wq + al256(sizeof(C) * (size_t)(lw > 0 ? lw : 1));
         const size_t need = o_we + al256(sizeof(cuDoubleComplex) * (size_t)(lw_e > 0 ? lw_e : 1));
         CKS_(grow_ws(h, &h->sub_ws, &h->sub_ws_bytes, true, need));
         char *ws = (char *)h->sub_ws;
-        cuComplex *Y = (cuComplex *)(ws + o_Y), *tau = (cuComplex *)(ws + o_tau), *B = (cuComplex *)(ws + o_B);
-        cuComplex *G = (cuComplex *)(ws + o_GP), *Mc = (cuComplex *)(ws + o_Mc);
-        cuDoubleComplex *GP = (cuDoubleComplex *)(ws + o_GP), *C = (cuDoubleComplex *)(ws + o_C);
+        C *Y = (C *)(ws + o_Y), *tau = (C *)(ws + o_tau), *B = (C *)(ws + o_B);
+        C *G = (C *)(ws + o_GP), *Mc = (C *)(ws + o_Mc);
+        cuDoubleComplex *GP = (cuDoubleComplex *)(ws + o_GP), *Cm = (cuDoubleComplex *)(ws + o_C);
         double *th = (double *)(ws + o_th), *rp = (double *)(ws + o_rp), *st = (double *)(ws + o_st);
         int *inf = (int *)(ws + o_inf);
-        cuComplex *wq = (cuComplex *)(ws + o_wq);
+        C *wq = (C *)(ws + o_wq);
         cuDoubleComplex *we = (cuDoubleComplex *)(ws + o_we);
         if (cudaMemsetAsync(inf, 0, sizeof(int) * 4, h->stream) != cudaSuccess) return OSMPS_ECUDA;
         // G (K x p), Y = M G
-        sub_random_kernel<<<h->nsm * 4, 256, 0, h->stream>>>((float2 *)G, (long long)K * p, 0x5EEDull + (unsigned)p);
+        sub_random_kernel<V2><<<h->nsm * 4, 256, 0, h->stream>>>((V2 *)G, (long long)K * p, 0x5EEDull + (unsigned)p);
         h->launches += 1;
-        cublasStatus_t bs =
-            colM ? g_blas.cgemm(g_blas.handle, CUBLAS_OP_N, CUBLAS_OP_N, n, p, K, &one, A, n, G, K, &zero, Y, n)
-                 : g_blas.cgemm(g_blas.handle, CUBLAS_OP_T, CUBLAS_OP_N, n, p, K, &one, A, K, G, K, &zero, Y, n);
+        cublasStatus_t bs = colM ? Lib::gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, p, K, &one, A, n, G, K, &zero, Y, n)
+                                 : Lib::gemm(CUBLAS_OP_T, CUBLAS_OP_N, n, p, K, &one, A, K, G, K, &zero, Y, n);
         if (bs != CUBLAS_STATUS_SUCCESS) return OSMPS_ECUDA;
         // Q = orth(Y), in place
-        if (g_solver.c_geqrf(g_solver.handle, n, p, Y, n, tau, wq, (int)lw, inf) != CUSOLVER_STATUS_SUCCESS ||
-            g_solver.c_ungqr(g_solver.handle, n, p, p, Y, n, tau, wq, (int)lw, inf + 1) != CUSOLVER_STATUS_SUCCESS)
-            return OSMPS_ECUDA;
+        if (!Lib::qr(n, p, Y, tau, wq, lw, inf)) return OSMPS_ECUDA;
         // B = Q^dag M (p x K)
-        bs = colM ? g_blas.cgemm(g_blas.handle, CUBLAS_OP_C, CUBLAS_OP_N, p, K, n, &one, Y, n, A, n, &zero, B, p)
-                  : g_blas.cgemm(g_blas.handle, CUBLAS_OP_C, CUBLAS_OP_T, p, K, n, &one, Y, n, A, K, &zero, B, p);
+        bs = colM ? Lib::gemm(CUBLAS_OP_C, CUBLAS_OP_N, p, K, n, &one, Y, n, A, n, &zero, B, p)
+                  : Lib::gemm(CUBLAS_OP_C, CUBLAS_OP_T, p, K, n, &one, Y, n, A, K, &zero, B, p);
         if (bs != CUBLAS_STATUS_SUCCESS) return OSMPS_ECUDA;
         // C = B B^dag in FP64 (lower triangle) and its eigenvalues
-        sub_gram64_kernel<<<dim3((unsigned)ntl, (unsigned)nsplit), 256, 0, h->stream>>>((const float2 *)B, p, (long long)K,
-                                                                                        nsplit, (double2 *)GP);
-        sub_gram_sum_kernel<<<h->nsm * 4, 256, 0, h->stream>>>((const double2 *)GP, p, nsplit, (double2 *)C);
+        sub_gram64_kernel<V2><<<dim3((unsigned)ntl, (unsigned)nsplit), 256, 0, h->stream>>>((const V2 *)B, p,
+                                                                                           (long long)K, nsplit,
+                                                                                           (double2 *)GP);
+        sub_gram_sum_kernel<<<h->nsm * 4, 256, 0, h->stream>>>((const double2 *)GP, p, nsplit, (double2 *)Cm);
         h->launches += 2;
-        if (g_solver.z_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, p, C, p, th, we,
+        if (g_solver.z_eig(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, p, Cm, p, th, we,
                            lw_e, inf + 2) != CUSOLVER_STATUS_SUCCESS)
             return OSMPS_ECUDA;
         // the weight outside the subspace: |M - Q B|_F^2
-        if (cudaMemcpyAsync(Mc, A, sizeof(cuComplex) * (size_t)n * K, cudaMemcpyDeviceToDevice, h->stream) !=
-            cudaSuccess)
+        if (cudaMemcpyAsync(Mc, A, sizeof(C) * (size_t)n * K, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
             return OSMPS_ECUDA;
-        bs = colM ? g_blas.cgemm(g_blas.handle, CUBLAS_OP_N, CUBLAS_OP_N, n, K, p, &mone, Y, n, B, p, &one, Mc, n)
-                  : g_blas.cgemm(g_blas.handle, CUBLAS_OP_T, CUBLAS_OP_T, K, n, p, &mone, B, p, Y, n, &one, Mc, K);
+        bs = colM ? Lib::gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, K, p, &mone, Y, n, B, p, &one, Mc, n)
+                  : Lib::gemm(CUBLAS_OP_T, CUBLAS_OP_T, K, n, p, &mone, B, p, Y, n, &one, Mc, K);
         if (bs != CUBLAS_STATUS_SUCCESS) return OSMPS_ECUDA;
-        sub_frob_kernel<<<kSubResBlocks, 256, 0, h->stream>>>((const float2 *)Mc, (long long)n * K, rp);
+        sub_frob_kernel<V2><<<kSubResBlocks, 256, 0, h->stream>>>((const V2 *)Mc, (long long)n * K, rp);
         h->launches += 1;
         int np = 0;
         if (launch_norm2(h, psi, h->partials, &np) != cudaSuccess) return OSMPS_ECUDA;
@@ -1400,7 +1460,7 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
             return OSMPS_ECUDA;
         if (!std::isfinite(hs[3])) return OSMPS_ENOCONV;  // solver status or a non-finite value
         const double trace = hs[0] + hs[1];
-        if (hs[0] <= 1e-9 * trace) {
+        if (hs[0] <= Lib::kResTol * trace) {
             // the next call starts from the values that mattered here, plus a quarter and 64
             const int cnt = (int)hs[2];
             h->sub_hint = cnt + cnt / 4 + 64;
@@ -1413,6 +1473,12 @@ osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambd
         }
         p = 2 * p < pmax ? 2 * p : pmax;
     }
+}
+
+osmps_status schmidt_subspace(Handle *h, const void *psi, int cut, double *lambda_dev, double *S_dev) {
+    if (!subspace_applicable(h, cut)) return OSMPS_EUNSUPPORTED;
+    return h->prec == OSMPS_FP64 ? schmidt_subspace_t<double>(h, psi, cut, lambda_dev, S_dev)
+                                 : schmidt_subspace_t<float>(h, psi, cut, lambda_dev, S_dev);
 }
 
 }  // namespace osmps

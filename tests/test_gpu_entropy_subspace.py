@@ -113,17 +113,45 @@ def test_subspace_quench_L24_against_fp64(steps):
     c.close()
 
 
-def test_subspace_not_for_fp64_or_small_blocks():
+def test_subspace_not_for_small_blocks():
     from paper_1802_10052_gb300 import OsmpsError
-    c = Chain(18, J=1.0, alpha=1.5, h=0.8, prec="fp64")
+    for prec in ("mixed", "fp64"):
+        c = Chain(16, J=1.0, alpha=1.5, h=0.8, prec=prec)  # 256 x 256 blocks: below the route's range
+        c.set_entropy_method(4)
+        x = to_dev(si.gaussian_state(16, 3), prec)
+        with pytest.raises(OsmpsError):
+            c.schmidt_entropy(x)
+        c.close()
+
+
+@pytest.mark.parametrize("L,cut", [(18, 9), (20, 10), (22, 13)])
+def test_subspace_fp64_matches_oracle(L, cut):
+    """complex128 quench states (the residual bound is 2e-12 of the trace there): S
+    within the FP64 tolerance of the oracle's S, the leading values within 1e-12."""
+    c, x = quench_state(L, 150, "fp64")
+    ref = x.cpu().numpy()
+    want = O.schmidt_spectrum_small(ref, L, cut)
+    S, lam = c.schmidt_entropy(x, cut=cut, spectrum=True)
+    assert abs(S - O.entropy_from_spectrum(want)) < TOL["fp64"]
+    np.testing.assert_allclose(lam[:32], want[:32], rtol=0, atol=1e-12)
+    assert abs(lam.sum() - np.sum(want)) < 1e-12
+    # a second call starts from the dimension the first one found (a different
+    # subspace): the same values to within the residual bound's share
     c.set_entropy_method(4)
-    x = to_dev(si.gaussian_state(18, 3), "fp64")
-    with pytest.raises(OsmpsError):
-        c.schmidt_entropy(x)
+    S4, lam4 = c.schmidt_entropy(x, cut=cut, spectrum=True)
+    assert abs(S4 - S) < 1e-11
     c.close()
-    c = Chain(16, J=1.0, alpha=1.5, h=0.8, prec="mixed")  # 256 x 256 blocks: below the route's range
-    c.set_entropy_method(4)
-    x = to_dev(si.gaussian_state(16, 3), "mixed")
-    with pytest.raises(OsmpsError):
-        c.schmidt_entropy(x)
+
+
+def test_subspace_fp64_falls_back_to_the_gram_route():
+    """A complex128 Gaussian state: the FP64 Gram eigenvalues."""
+    L = 18
+    c = Chain(L, J=1.0, alpha=1.0, h=1.0, prec="fp64")
+    x = to_dev(si.gaussian_state(L, 41), "fp64")
+    want = O.schmidt_spectrum_small(x.cpu().numpy(), L, 9)
+    S, lam = c.schmidt_entropy(x, spectrum=True)
+    np.testing.assert_allclose(lam, want, rtol=0, atol=1e-13)
+    assert abs(S - O.entropy_from_spectrum(want)) < TOL["fp64"]
+    c.set_entropy_method(0)
+    assert c.schmidt_entropy(x) == S
     c.close()
