@@ -134,7 +134,8 @@ def test_subspace_fp64_matches_oracle(L, cut):
     S, lam = c.schmidt_entropy(x, cut=cut, spectrum=True)
     assert abs(S - O.entropy_from_spectrum(want)) < TOL["fp64"]
     np.testing.assert_allclose(lam[:32], want[:32], rtol=0, atol=1e-12)
-    assert abs(lam.sum() - np.sum(want)) < 1e-12
+    # the values hold all but the uncaptured weight, at most 2e-12 of the trace
+    assert abs(lam.sum() - np.sum(want)) < 2e-12 + 1e-14
     # a second call starts from the dimension the first one found (a different
     # subspace): the same values to within the residual bound's share
     c.set_entropy_method(4)
