@@ -290,12 +290,14 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
     __shared__ int s_int[2];
     __shared__ double s_dbl[2];
     __shared__ double s_slot[2][4];  // cluster reductions, double-buffered
+    __shared__ unsigned s_fxe;       // complex128: the current tile's largest FP64 exponent
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int csize = cluster_size(), crank = cluster_rank();
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fxe = 0u;
     }
     __syncthreads();
     if (csize > 1) cluster_barrier();  // peers' shared memory exists before any remote access
@@ -461,6 +463,33 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
                 constexpr int HV = kVPT / 2;  // vectors per half
                 T part1 = (T)0, part2 = (T)0;
                 V *dt = dst + (size_t)t * kTileVec;
+                // complex128: the flip sums in 64-bit fixed point on the tile's grid
+                // (exact integer adds; the FP64 pipe keeps the diagonal and the dots)
+                int et = 0;
+                double fxs = 0.0;
+                if constexpr (sizeof(T) == sizeof(double)) {
+                    unsigned em = 0u;
+#pragma unroll
+                    for (int q = 0; q < NE; ++q) em = max(em, max(fx_expo(tocx(self[q]).x), fx_expo(tocx(self[q]).y)));
+                    em = __reduce_max_sync(0xffffffffu, em);
+                    if (lane == 0) atomicMax(&s_fxe, em);
+                    __syncthreads();
+                    et = (int)*reinterpret_cast<volatile unsigned *>(&s_fxe);
+                    fxs = fx_scale((double)hT * sc, et);
+                    longlong2 *Ux = reinterpret_cast<longlong2 *>(const_cast<V *>(Us));
+#pragma unroll
+                    for (int i = 0; i < kVPT; ++i) {
+                        const double2 a = tocx(self[i]);
+                        longlong2 f;
+                        f.x = fx_from(a.x, et);
+                        f.y = fx_from(a.y, et);
+                        Ux[tid + kThreads * i] = f;
+                    }
+                    // generic-proxy stores ordered before the stage's next bulk copy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                    if (tid == 0) s_fxe = 0u;  // read by every thread; the next tile starts after a barrier
+                }
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     A acc[HV * VE];
@@ -482,22 +511,54 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
                             afma(hk, self[gi * VE], acc[i * VE + VE - 1]);
                         }
                     }
+                    if constexpr (sizeof(T) == sizeof(double)) {
+                        const longlong2 *Ux = reinterpret_cast<const longlong2 *>(Us);
+                        long long ar[HV], ai[HV];
 #pragma unroll
-                    for (int kb = 0; kb < 4; ++kb)
+                        for (int i = 0; i < HV; ++i) ar[i] = ai[i] = 0ll;
 #pragma unroll
-                        for (int i = 0; i < HV; ++i)
+                        for (int kb = 0; kb < 4; ++kb)
 #pragma unroll
-                            for (int e = 0; e < VE; ++e)
-                                afma(hk, self[((hh * HV + i) ^ (1 << kb)) * VE + e], acc[i * VE + e]);
+                            for (int i = 0; i < HV; ++i) {
+                                const longlong2 v = Ux[tid + kThreads * ((hh * HV + i) ^ (1 << kb))];
+                                ar[i] += v.x;
+                                ai[i] += v.y;
+                            }
 #pragma unroll 1
-                    for (int kb = 0; kb < 8; ++kb) {
-                        const int pt = tid ^ (1 << kb);
+                        for (int kb = 0; kb < 8; ++kb) {
+                            const longlong2 *Uf = Ux + (tid ^ (1 << kb));
+#pragma unroll
+                            for (int i = 0; i < HV; ++i) {
+                                const longlong2 v = Uf[kThreads * (hh * HV + i)];
+                                ar[i] += v.x;
+                                ai[i] += v.y;
+                            }
+                        }
 #pragma unroll
                         for (int i = 0; i < HV; ++i) {
-                            A pv[VE];
-                            unpackv(Us[pt + kThreads * (hh * HV + i)], pv);
+                            double2 a = tocx(acc[i]);
+                            a.x = fma(fxs, __ll2double_rn(ar[i]), a.x);
+                            a.y = fma(fxs, __ll2double_rn(ai[i]), a.y);
+                            acc[i] = a;
+                        }
+                    } else {
 #pragma unroll
-                            for (int e = 0; e < VE; ++e) afma(hk, pv[e], acc[i * VE + e]);
+                        for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+                            for (int i = 0; i < HV; ++i)
+#pragma unroll
+                                for (int e = 0; e < VE; ++e)
+                                    afma(hk, self[((hh * HV + i) ^ (1 << kb)) * VE + e], acc[i * VE + e]);
+#pragma unroll 1
+                        for (int kb = 0; kb < 8; ++kb) {
+                            const int pt = tid ^ (1 << kb);
+#pragma unroll
+                            for (int i = 0; i < HV; ++i) {
+                                A pv[VE];
+                                unpackv(Us[pt + kThreads * (hh * HV + i)], pv);
+#pragma unroll
+                                for (int e = 0; e < VE; ++e) afma(hk, pv[e], acc[i * VE + e]);
+                            }
                         }
                     }
                     if (mode == MODE_RESID) {

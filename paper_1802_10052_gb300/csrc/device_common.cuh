@@ -77,6 +77,37 @@ static __device__ __forceinline__ double warp_sum_partials(const double *partial
     return s;
 }
 
+// ---- complex128 flip sums in 64-bit fixed point ----
+// All amplitudes of a tile go on one grid of unit 2^(et - 1080), et the largest
+// biased FP64 exponent in the tile, so every |X| < 2^58 and the sum of a
+// partner per flipped bit (at most 12) is exact in 64-bit integers.  Onto the
+// grid by integer operations; back by one conversion, the unit folded into the
+// field: the FP64 pipe (2 lanes per clock per SM on this part) is left to the
+// diagonal, the partial sum and the epilogue.
+static __device__ __forceinline__ unsigned fx_expo(double x) {
+    return (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu;
+}
+// x on the grid, truncated toward zero (error below one unit, i.e. below
+// 2^-57 of the tile's largest magnitude); zero and subnormals give 0
+static __device__ __forceinline__ long long fx_from(double x, int et) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(((unsigned long long)b >> 52) & 0x7FFull);
+    const unsigned long long M = (((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << 5;
+    const int sh = et - e;  // >= 0
+    unsigned long long a = sh < 64 ? (M >> sh) : 0ull;
+    if (e == 0) a = 0ull;
+    const long long sg = b >> 63;  // 0 or -1
+    return ((long long)a ^ sg) - sg;
+}
+// the field times the grid unit: one FP64 multiply per value turns an integer
+// sum (converted with rounding to nearest) into its term; tiles whose largest
+// magnitude is under 2^-960 get 0, a non-finite amplitude in the tile NaN
+static __device__ __forceinline__ double fx_scale(double h, int et) {
+    if (et >= 2047) return __longlong_as_double(0x7FF8000000000000ll);
+    if (et <= 57) return 0.0;
+    return h * __longlong_as_double((long long)(et - 57) << 52);
+}
+
 // ---- mbarrier / TMA primitives (PTX) ----
 __device__ __forceinline__ unsigned smem_u32(const void *ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
