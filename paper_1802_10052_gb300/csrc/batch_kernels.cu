@@ -609,29 +609,86 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
                 for (int i = 0; i < kVPT; ++i) unpackv(dst[gvec(m, i)], &wv[i * VE]);  // partial sum of pass A
 #pragma unroll
                 for (int q = 0; q < NE; ++q) f[q] = azero((T)0);
-                // flips of tile-local bits c .. TBITS-1, partners read from shared memory
+                bool fx_done = false;
+                if constexpr (sizeof(T) == sizeof(double)) {
+                    if (TBITS - c >= 4) {
+                        // complex128, four or more gathered bits: the flip sums in
+                        // 64-bit fixed point on the tile's grid, as in pass A
+                        unsigned em = 0u;
+#pragma unroll
+                        for (int i = 0; i < kVPT; ++i) {
+                            const double2 a = tocx(Us[tid + kThreads * i]);
+                            em = max(em, max(fx_expo(a.x), fx_expo(a.y)));
+                        }
+                        em = __reduce_max_sync(0xffffffffu, em);
+                        if (lane == 0) atomicMax(&s_fxe, em);
+                        __syncthreads();
+                        const int et = (int)*reinterpret_cast<volatile unsigned *>(&s_fxe);
+                        const double fxs = fx_scale((double)hT * sc, et);
+                        longlong2 *Ux = reinterpret_cast<longlong2 *>(const_cast<V *>(Us));
+                        longlong2 own[kVPT];
+#pragma unroll
+                        for (int i = 0; i < kVPT; ++i) {
+                            const double2 a = tocx(Us[tid + kThreads * i]);
+                            own[i].x = fx_from(a.x, et);
+                            own[i].y = fx_from(a.y, et);
+                        }
+                        __syncthreads();  // every thread has read its doubles before any is overwritten
+#pragma unroll
+                        for (int i = 0; i < kVPT; ++i) Ux[tid + kThreads * i] = own[i];
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncthreads();
+                        if (tid == 0) s_fxe = 0u;
+                        long long ar[kVPT], ai[kVPT];
+#pragma unroll
+                        for (int i = 0; i < kVPT; ++i) ar[i] = ai[i] = 0ll;
 #pragma unroll 1
-                for (int kb = 0; kb < 12; ++kb) {
-                    if (LOGVE + kb < c) continue;
-                    const int pb = kb < 8 ? (1 << kb) : (kThreads << (kb - 8));  // partner offset in vectors
+                        for (int kb = c; kb < TBITS; ++kb) {
+                            const int pb = kb < 8 ? (1 << kb) : (kThreads << (kb - 8));  // partner offset in vectors
 #pragma unroll
-                    for (int i = 0; i < kVPT; ++i) {
-                        A pv[VE];
-                        unpackv(Us[(tid + kThreads * i) ^ pb], pv);
+                            for (int i = 0; i < kVPT; ++i) {
+                                const longlong2 v = Ux[(tid + kThreads * i) ^ pb];
+                                ar[i] += v.x;
+                                ai[i] += v.y;
+                            }
+                        }
 #pragma unroll
-                        for (int e = 0; e < VE; ++e) afma(hk, pv[e], f[i * VE + e]);
+                        for (int i = 0; i < kVPT; ++i) {
+                            double2 a = tocx(wv[i]);
+                            a.x = fma(fxs, __ll2double_rn(ar[i]), a.x);
+                            a.y = fma(fxs, __ll2double_rn(ai[i]), a.y);
+                            wv[i] = a;
+                        }
+                        fx_done = true;
                     }
                 }
-                T part1 = (T)0, part2 = (T)0;
-                const K one = mkcoef((T)1);
+                if (!fx_done) {
+                    // flips of tile-local bits c .. TBITS-1, partners read from shared memory
+#pragma unroll 1
+                    for (int kb = 0; kb < 12; ++kb) {
+                        if (LOGVE + kb < c) continue;
+                        const int pb = kb < 8 ? (1 << kb) : (kThreads << (kb - 8));  // partner offset in vectors
 #pragma unroll
-                for (int q = 0; q < NE; ++q) afma(one, f[q], wv[q]);
+                        for (int i = 0; i < kVPT; ++i) {
+                            A pv[VE];
+                            unpackv(Us[(tid + kThreads * i) ^ pb], pv);
+#pragma unroll
+                            for (int e = 0; e < VE; ++e) afma(hk, pv[e], f[i * VE + e]);
+                        }
+                    }
+                    const K one = mkcoef((T)1);
+#pragma unroll
+                    for (int q = 0; q < NE; ++q) afma(one, f[q], wv[q]);
+                }
+                T part1 = (T)0, part2 = (T)0;
                 if (mode == MODE_RESID) {
                     const K mth = mkcoef(-thT);
 #pragma unroll
                     for (int i = 0; i < kVPT; ++i) {
                         A sv[VE];
-                        unpackv(Us[tid + kThreads * i], sv);
+                        // the tile holds integers after a fixed-point pass: u from global
+                        // memory then (the same values, just staged from there)
+                        unpackv(fx_done ? src[gvec(m, i)] : Us[tid + kThreads * i], sv);
 #pragma unroll
                         for (int e = 0; e < VE; ++e) {
                             part2 += adot(sv[e], wv[i * VE + e]);
@@ -647,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 1) lanczos_batch_kernel(BatchParams<
 #pragma unroll
                         for (int i = 0; i < kVPT; ++i) {
                             A sv[VE];
-                            unpackv(Us[tid + kThreads * i], sv);
+                            unpackv(fx_done ? src[gvec(m, i)] : Us[tid + kThreads * i], sv);
 #pragma unroll
                             for (int e = 0; e < VE; ++e) part1 += adot(sv[e], wv[i * VE + e]);
                         }
