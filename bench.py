@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-rdm", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-scale", action="store_true")
+    ap.add_argument("--no-entropy-routes", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--entropy", choices=["async", "sync"], default="sync",
                     help="bond entropy per step: overlapped eigen-solve (async) or blocking (sync)")
@@ -583,6 +584,44 @@ def rdm_L24(reps=3):
             "entropy_sweep_ms": t_sweep * 1e3}
 
 
+def entropy_routes_L24(times=(0.5, 1.0, 2.5)):
+    """Half-chain entropy of the L = 24 quench state (complex64) at a few times: ms per
+    measurement on the dominant subspace (method 4, the default; second call on the
+    handle, so it starts from the dimension the first found) and on the full route
+    (Gram eigenvectors, Rayleigh quotients; method 2), and |dS| between them."""
+    import numpy as np
+    import torch
+
+    from paper_1802_10052_gb300 import Chain
+
+    c = Chain(24, J=1.0, alpha=1.5, h=0.8, prec="mixed")
+    x = c.new_state()
+    c.init_basis_state(x, 0)
+    t = 0.0
+    out = {"workload": "L=24 quench state (alpha=1.5, h=0.8, all up, Krylov m=20 dt=0.01), complex64, cut 12|12",
+           "points": []}
+
+    def timed(method):
+        c.set_entropy_method(method)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S, lam = c.schmidt_entropy(x, spectrum=True)
+        return S, lam, (time.perf_counter() - t0) * 1e3
+
+    for target in times:
+        steps = int(round((target - t) / 0.01))
+        c.krylov_evolve(x, 0.01, steps, 20)
+        t = target
+        timed(4)
+        S4, lam4, ms4 = timed(4)
+        timed(2)  # the library solver's first call sets itself up
+        S2, lam2, ms2 = timed(2)
+        out["points"].append({"t": t, "subspace_ms": ms4, "full_ms": ms2, "S": S4, "abs_dS": abs(S4 - S2),
+                              "values_above_1e-12": int(np.sum(lam4 > 1e-12))})
+    c.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -917,6 +956,11 @@ def main():
         extra["rdm_L24"] = rdm_L24()
     if rank == 0 and not args.no_scale:
         extra["scale_L30"] = scale_L30()
+    if rank == 0 and not args.no_entropy_routes:
+        try:
+            extra["entropy_routes_L24"] = entropy_routes_L24()
+        except Exception as e:  # a leg of context: never the headline's failure
+            extra["entropy_routes_L24"] = {"error": repr(e)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_line()
