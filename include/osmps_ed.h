@@ -57,7 +57,7 @@ typedef enum {
     OSMPS_ECUDA = 3,        /* a CUDA runtime or library call failed */
     OSMPS_ENOCONV = 4,      /* Lanczos did not reach the tolerance in max_iter */
     OSMPS_ETIMEOUT = 5,     /* a bounded device wait gave up */
-    OSMPS_EUNSUPPORTED = 6  /* valid request this build does not support */
+    OSMPS_EUNSUPPORTED = 6  /* valid request the library does not support here */
 } osmps_status;
 
 typedef enum {
