@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--main-priority", choices=["high", "default"], default="high",
                     help="priority of the stream the evolution runs on")
     ap.add_argument("--profile-case", choices=["batch_L16", "gates_L24", "rdm_L24", "hpsi_L27", "quench_L24",
-                                               "hpsi_fp64_L24", "krylov_L24"],
+                                               "hpsi_fp64_L24", "krylov_L24", "entropy_L24"],
                     default=None,
                     help="run one small profiling workload and exit (for ncu captures)")
     return ap.parse_args()
@@ -846,6 +846,18 @@ def profile_case(name):
             c.apply_H(x, y)
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": name, "norm": float(torch.linalg.vector_norm(y).item())}))
+        c.close()
+    elif name == "entropy_L24":
+        # the half-chain entropy of the L = 24 quench state at t = 1 (complex64, default
+        # route: the dominant subspace, p = 128), three calls
+        from paper_1802_10052_gb300 import Chain
+        c = Chain(WL["L"], J=WL["J"], alpha=WL["alpha"], h=WL["h"], prec="mixed")
+        x = c.new_state()
+        c.init_basis_state(x, 0)
+        c.krylov_evolve(x, WL["dt"], 100, WL["m"])
+        S = [c.schmidt_entropy(x) for _ in range(3)]
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "S": S}))
         c.close()
     elif name == "krylov_L24":
         # one Krylov step (m = 20) of the L = 24 quench state at t = 0.1, complex64: 20 products

@@ -1389,11 +1389,20 @@ static osmps_status schmidt_subspace_t(Handle *h, const void *psi, int cut, doub
             g_solver.z_bufsize(g_solver.handle, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, p,
                                (const cuDoubleComplex *)A, p, (const double *)A, &lw_e) != CUSOLVER_STATUS_SUCCESS)
             return OSMPS_ECUDA;
-        // lower-triangle tiles of C and the K split that fills the GPU
+        // lower-triangle tiles of C and the K split with the shortest makespan: waves of
+        // one CTA per SM, each CTA a 1/nsplit share of K (a split that leaves a few
+        // SMs a second CTA doubles the kernel's time)
         const int nt = (p + kG64T - 1) / kG64T, ntl = nt * (nt + 1) / 2;
-        int nsplit = (2 * h->nsm + ntl - 1) / ntl;
-        if (nsplit > 16) nsplit = 16;
-        if (nsplit < 1) nsplit = 1;
+        int nsplit = 1;
+        double best = 1e300;
+        for (int ns = 1; ns <= 16; ++ns) {
+            const long long waves = ((long long)ntl * ns + h->nsm - 1) / h->nsm;
+            const double cost = (double)waves / ns;
+            if (cost < best - 1e-12) {
+                best = cost;
+                nsplit = ns;
+            }
+        }
         const size_t gpart = sizeof(cuDoubleComplex) * (size_t)nsplit * p * p;
         const size_t gk = sizeof(C) * (size_t)p * K;  // G (K x p) before B
         const size_t o_Y = 0;
